@@ -1,0 +1,205 @@
+/*
+ * libvie -- GB300-native circulant-preconditioned voxel VIE solver (C ABI).
+ *
+ * Problem (Groth, Polimeridis, Tambova, White, "Circulant preconditioning in
+ * the volume integral equation method for silicon photonics", Sec. 2,
+ * Eqs. JVIE and discrete_form): on a uniform grid of nx*ny*nz cubic voxels of
+ * edge h, solve
+ *
+ *      (I - M N) w = M e_inc,        M = (eps_r - 1)/eps_r  per voxel,
+ *
+ * for the normalised polarisation current w = j / (j omega eps0).  eps_r is
+ * the permittivity relative to the background eps_bg (Table 1, "Si in SiO2"),
+ * N = I + G is the Galerkin JVIE operator with the background wavenumber
+ * k_b = k0 sqrt(eps_bg), time dependence exp(+j omega t), eps = eps' - j eps''.
+ * G's entries: one-point rule between distinct voxels and the equal-volume
+ * sphere self term (the paper does not print its singular integrals).
+ *
+ * Layouts (all arrays C-ordered, x fastest):
+ *   scalar voxel field   [nz][ny][nx]           complex (double2: re, im)
+ *   vector voxel field   [3][nz][ny][nx]        components x, y, z
+ *
+ * Ownership: every pointer argument marked "device" must point to memory of
+ * the device that is current when the plan is created, allocated and freed by
+ * the caller.  "host" pointers are ordinary (preferably pinned) host memory.
+ * The library owns everything inside a plan (generator spectra, material
+ * arrays, preconditioner blocks, Krylov workspace); it allocates only in
+ * vie_plan_create, vie_build_preconditioner and vie_server_* calls, never
+ * inside vie_matvec / vie_precond_apply / vie_solve.
+ *
+ * Streams: every call enqueues its GPU work on the stream given at plan
+ * creation (NULL = legacy default stream).  vie_matvec and vie_precond_apply
+ * return without synchronising; vie_build_preconditioner and vie_solve
+ * synchronise that stream before returning.
+ *
+ * Errors: every call returns a vie_status.  Negative values are hard errors
+ * (the message is available from vie_last_error() on the calling thread);
+ * VIE_ENOCONV (1) means the solver stopped at its iteration limit and the
+ * best iterate was written.  No call throws or aborts.
+ */
+#ifndef LIBVIE_VIE_H
+#define LIBVIE_VIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VIE_OK = 0,
+  VIE_ENOCONV = 1,      /* iteration limit reached; best iterate returned     */
+  VIE_PENDING = 2,      /* vie_server_poll: request not finished yet          */
+  VIE_EINVAL = -1,      /* invalid argument or unsupported size               */
+  VIE_ENOMEM = -2,      /* device or host allocation failed                   */
+  VIE_ECUDA = -3,       /* CUDA runtime error                                 */
+  VIE_ETIMEOUT = -4,    /* a bounded wait ran out                             */
+  VIE_EREJECTED = -5,   /* server admission refused the request               */
+  VIE_ESTATE = -6       /* call out of order (e.g. solve before permittivity)  */
+} vie_status;
+
+typedef enum { VIE_FP64 = 0, VIE_MIXED = 1 } vie_precision;
+
+/* Homogenisation of M for the preconditioner, Sec. 5.2 (three variants). */
+typedef enum { VIE_HOM_MODE = 1, VIE_HOM_MEAN = 2, VIE_HOM_REALMEAN = 3 } vie_homog;
+
+/* Preconditioner: none (identity) or the 1-level circulant of Sec. 4. */
+typedef enum { VIE_PREC_NONE = 0, VIE_PREC_CIRCULANT = 1 } vie_precond_kind;
+
+/* Axis-aligned partition box in voxel indices (Sec. 5.3). */
+typedef struct { int x0, y0, z0, nx, ny, nz; } vie_box;
+
+typedef struct {
+  int restart;            /* GMRES restart length (default 50)                      */
+  double tol;             /* stop at ||b - A w||_2 / ||b||_2 <= tol (FP64 residual) */
+  int max_iter;           /* cap on total GMRES iterations (all restarts/refinements)*/
+  double inner_tol;       /* mixed: relative tolerance of each inner c64 GMRES      */
+  int max_refine;         /* mixed: cap on FP64 iterative-refinement steps          */
+  int precision;          /* vie_precision                                          */
+  int precond;            /* vie_precond_kind                                       */
+  int homog;              /* vie_homog                                              */
+  double reduce_tol;      /* memory reduction threshold tau (Sec. 5.1.1); 0 = off   */
+  const vie_box* boxes;   /* partition boxes (copied at plan creation); NULL = one  */
+  int nboxes;             /*   box covering the whole grid                          */
+} vie_opts;
+
+typedef struct {
+  int iters_inner;        /* total GMRES iterations                                  */
+  int iters_outer;        /* FP64 refinement steps (1 for VIE_FP64)                  */
+  double relres;          /* final ||b - A w|| / ||b|| computed in FP64              */
+  size_t precond_bytes;   /* device bytes held by the preconditioner blocks          */
+  double kept_fraction;   /* kept blocks / total frequencies over all boxes          */
+  float t_setup_ms;       /* preconditioner build time of the last build             */
+  float t_solve_ms;       /* wall time of the last solve                             */
+} vie_info;
+
+typedef struct vie_plan_s* vie_plan_t;
+
+/* Fill *opts with the defaults: restart 50, tol 1e-9, max_iter 5000,
+ * inner_tol 1e-4, max_refine 20, VIE_MIXED, VIE_PREC_CIRCULANT,
+ * VIE_HOM_REALMEAN, reduce_tol 1e-3, whole-grid box. */
+void vie_default_opts(vie_opts* opts);
+
+/* Create a plan for an nx*ny*nz grid of voxel edge h (same length unit as
+ * 1/k0), free-space wavenumber k0 and background permittivity eps_bg (Sec. 2;
+ * Eq. sys_mat).  Assembles the 6 unique Green's generators in FP64 and
+ * stores their circulant-embedding spectra (the O(6n) storage of the remark
+ * after Eq. sys_mat).  cuda_stream: a cudaStream_t or NULL.  opts may be
+ * NULL (defaults).  Boxes must lie inside the grid and not overlap.
+ * Errors: VIE_EINVAL for non-positive sizes, h, k0 or eps_bg, or boxes out of
+ * range / overlapping; VIE_ENOMEM if device memory runs out. */
+vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double eps_bg,
+                           const vie_opts* opts, void* cuda_stream, vie_plan_t* out);
+
+/* Release every device and host resource of the plan (NULL is ignored). */
+void vie_plan_destroy(vie_plan_t plan);
+
+/* Set the relative permittivity eps_r = eps' - j eps'' (device, double2,
+ * [nz][ny][nx], relative to vacuum; eps' > 0).  Computes M (Sec. 2) on the
+ * device.  Invalidates a previously built preconditioner. */
+vie_status vie_set_permittivity(vie_plan_t plan, const void* eps_dev);
+
+/* Build the block-diagonal 1-level circulant preconditioner of Sec. 4 / 5.3:
+ * per box, homogenise M (Sec. 5.2), form the Chan eigenvalues (Eq. Chan and
+ * the diagonalisation C = F^-1 Lambda F), assemble the per-frequency blocks
+ * D_f (Eq. Di), select the kept blocks (Eqs. proxy1-proxy2) when
+ * reduce_tol > 0, and factor every kept block by FP64 LU with partial
+ * pivoting; the inverse is stored in complex FP32 (mixed) and/or FP64.
+ * Synchronises the plan stream.  No-op for VIE_PREC_NONE. */
+vie_status vie_build_preconditioner(vie_plan_t plan);
+
+/* y = A x = x - M (x + G x) (Eq. discrete_form) for device vectors x, y
+ * ([3][nz][ny][nx] double2; may not alias).  precision VIE_FP64 computes in
+ * complex FP64; VIE_MIXED rounds x to complex FP32, applies the FP32 operator
+ * and widens the result.  Asynchronous on the plan stream. */
+vie_status vie_matvec(vie_plan_t plan, const void* x_dev, void* y_dev, int precision);
+
+/* z = P^{-1} r with the built preconditioner (identity outside the boxes),
+ * device vectors [3][nz][ny][nx] double2 (no aliasing).  precision as for
+ * vie_matvec.  VIE_ESTATE if the preconditioner was not built. */
+vie_status vie_precond_apply(vie_plan_t plan, const void* r_dev, void* z_dev, int precision);
+
+/* Solve (I - M N) w = M e_inc (Sec. 2) with right-preconditioned GMRES
+ * (restart opts.restart).  VIE_FP64: complex FP64 throughout.  VIE_MIXED:
+ * complex FP32 GMRES inside FP64 iterative refinement.  e_inc and w_out are
+ * device [3][nz][ny][nx] double2.  Builds the preconditioner if needed.
+ * info may be NULL.  Synchronises the plan stream. */
+vie_status vie_solve(vie_plan_t plan, const void* e_inc_dev, void* w_out_dev, vie_info* info);
+
+/* As vie_set_permittivity + vie_solve, with host buffers: copies eps and
+ * e_inc to the device, solves and copies w back (host, double2 arrays). */
+vie_status vie_solve_host(vie_plan_t plan, const void* eps_host, const void* e_inc_host,
+                          void* w_out_host, vie_info* info);
+
+/* Solve n independent problems (each plan already has its permittivity),
+ * overlapping them on the device: plan i's work runs on its own stream.
+ * e_inc[i], w_out[i] are device pointers; info may be NULL or an array of n.
+ * Returns the most severe status. */
+vie_status vie_solve_batch(vie_plan_t* plans, int n, const void* const* e_inc_dev,
+                           void* const* w_out_dev, vie_info* info);
+
+/* Continuous-batching server.  Requests are admitted while their estimated
+ * device footprint fits in budget_bytes and fewer than max_inflight are
+ * running; each admitted request runs on its own stream/worker and overlaps
+ * the others.  A request that can never fit is rejected (VIE_EREJECTED). */
+typedef struct vie_server_s* vie_server_t;
+
+vie_status vie_server_create(size_t budget_bytes, int max_inflight, vie_server_t* out);
+
+/* Submit one solve: grid/physics as in vie_plan_create, permittivity and
+ * incident field as HOST double2 arrays (copied before return), result to
+ * the HOST array w_out (written before the request reports VIE_OK).
+ * *ticket receives the request id. */
+vie_status vie_server_submit(vie_server_t srv, int nx, int ny, int nz, double h, double k0,
+                             double eps_bg, const vie_opts* opts, const void* eps_host,
+                             const void* e_inc_host, void* w_out_host, int64_t* ticket);
+
+/* VIE_OK (finished, *info filled), VIE_PENDING, or the request's error. */
+vie_status vie_server_poll(vie_server_t srv, int64_t ticket, vie_info* info);
+
+/* Block until every submitted request has finished or timeout_ms elapses
+ * (VIE_ETIMEOUT). */
+vie_status vie_server_drain(vie_server_t srv, double timeout_ms);
+
+/* Bytes currently reserved by admitted requests. */
+size_t vie_server_reserved_bytes(vie_server_t srv);
+
+/* Estimated device bytes of a plan with these sizes and options (used by
+ * admission control). */
+size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts);
+
+void vie_server_destroy(vie_server_t srv);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* vie_last_error(void);
+
+/* Number of kernels this library has launched in this process (all plans);
+ * used to report launch counts. */
+int64_t vie_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBVIE_VIE_H */

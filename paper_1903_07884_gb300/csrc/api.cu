@@ -1,0 +1,493 @@
+// C ABI of libvie: plan lifecycle, matvec / preconditioner hooks, solves,
+// batched solves and the continuous-batching server.
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace vie {
+
+static thread_local char g_err[1024] = "";
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// Stream-ordered allocations on the calling plan's stream: no device-wide
+// synchronisation, so concurrent requests keep overlapping.
+vie_status DevBuf::alloc(size_t n) {
+  release();
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMallocAsync(&p, n, g_alloc_stream);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    set_error("device allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    return VIE_ENOMEM;
+  }
+  bytes = n;
+  stream = g_alloc_stream;
+  return VIE_OK;
+}
+
+void DevBuf::release() {
+  if (p) cudaFreeAsync(p, stream);
+  p = nullptr;
+  bytes = 0;
+}
+
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~StreamScope() { g_alloc_stream = prev; }
+};
+
+static std::once_flag g_pool_once;
+static void init_pool() {
+  std::call_once(g_pool_once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+static bool boxes_valid(int nx, int ny, int nz, const std::vector<vie_box>& bs) {
+  for (size_t i = 0; i < bs.size(); ++i) {
+    const vie_box& b = bs[i];
+    if (b.nx < 1 || b.ny < 1 || b.nz < 1 || b.x0 < 0 || b.y0 < 0 || b.z0 < 0) return false;
+    if (b.x0 + b.nx > nx || b.y0 + b.ny > ny || b.z0 + b.nz > nz) return false;
+    for (size_t j = 0; j < i; ++j) {
+      const vie_box& c = bs[j];
+      const bool ox = b.x0 < c.x0 + c.nx && c.x0 < b.x0 + b.nx;
+      const bool oy = b.y0 < c.y0 + c.ny && c.y0 < b.y0 + b.ny;
+      const bool oz = b.z0 < c.z0 + c.nz && c.z0 < b.z0 + b.nz;
+      if (ox && oy && oz) return false;
+    }
+  }
+  return true;
+}
+
+static int embed_len(int n) { return 2 * fft_next_smooth(n); }
+
+}  // namespace vie
+
+using namespace vie;
+
+extern "C" {
+
+void vie_default_opts(vie_opts* o) {
+  if (!o) return;
+  o->restart = 50;
+  o->tol = 1e-9;
+  o->max_iter = 5000;
+  o->inner_tol = 1e-4;
+  o->max_refine = 20;
+  o->precision = VIE_MIXED;
+  o->precond = VIE_PREC_CIRCULANT;
+  o->homog = VIE_HOM_REALMEAN;
+  o->reduce_tol = 1e-3;
+  o->boxes = nullptr;
+  o->nboxes = 0;
+}
+
+const char* vie_last_error(void) { return g_err; }
+
+int64_t vie_kernel_launches(void) { return (int64_t)launches_total(); }
+
+vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double eps_bg, const vie_opts* opts,
+                           void* cuda_stream, vie_plan_t* out) {
+  if (!out) { set_error("vie_plan_create: out is NULL"); return VIE_EINVAL; }
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0) || !(k0 >= 0) || !(eps_bg > 0)) {
+    set_error("vie_plan_create: invalid grid or physics (nx=%d ny=%d nz=%d h=%g k0=%g eps_bg=%g)", nx, ny, nz, h, k0,
+              eps_bg);
+    return VIE_EINVAL;
+  }
+  init_pool();
+  std::unique_ptr<vie_plan_s> P(new vie_plan_s());
+  P->nx = nx; P->ny = ny; P->nz = nz;
+  P->h = h; P->k0 = k0; P->eps_bg = eps_bg;
+  P->kb = k0 * sqrt(eps_bg);
+  if (opts) P->opts = *opts; else vie_default_opts(&P->opts);
+  vie_opts& o = P->opts;
+  if (o.restart < 1 || o.restart > 128 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 1 ||
+      (o.precision != VIE_FP64 && o.precision != VIE_MIXED) ||
+      (o.precond != VIE_PREC_NONE && o.precond != VIE_PREC_CIRCULANT) || o.homog < 1 || o.homog > 3 ||
+      !(o.reduce_tol >= 0) || !(o.inner_tol > 0) || o.nboxes < 0 || (o.nboxes > 0 && !o.boxes)) {
+    set_error("vie_plan_create: invalid options");
+    return VIE_EINVAL;
+  }
+  if (o.nboxes > 0) P->boxes.assign(o.boxes, o.boxes + o.nboxes);
+  else P->boxes.push_back(vie_box{0, 0, 0, nx, ny, nz});
+  o.boxes = nullptr;
+  o.nboxes = (int)P->boxes.size();
+  if (!boxes_valid(nx, ny, nz, P->boxes)) { set_error("vie_plan_create: boxes out of range or overlapping"); return VIE_EINVAL; }
+  P->st = (cudaStream_t)cuda_stream;
+  VIE_CUDA(cudaGetDevice(&P->device));
+  StreamScope scope(P->st);
+  MvDims& d = P->d;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.L = embed_len(nx); d.Py = embed_len(ny); d.Pz = embed_len(nz);
+  d.Lh = d.L / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
+  if ((long long)d.Py * d.Pz > 4096) { set_error("vie_plan_create: cross-section too large (Py*Pz > 4096)"); return VIE_EINVAL; }
+  if (d.L > fft_max_len<double2>()) {
+    set_error("vie_plan_create: nx=%d needs an x-embedding of %d > %d points", nx, d.L, fft_max_len<double2>());
+    return VIE_EINVAL;
+  }
+  for (const vie_box& b : P->boxes) {
+    const FftLen* f;
+    VIE_TRY(fft_get(b.nx, &f));
+    const int lim = o.precision == VIE_FP64 ? fft_max_len<double2>() : fft_max_len<float2>();
+    const int len = f->bluestein ? f->M : f->n;
+    if (len > lim || (f->bluestein && len > fft_max_len<double2>())) {
+      set_error("vie_plan_create: box length %d needs a transform of %d points (limit %d)", b.nx, len,
+                fft_max_len<double2>());
+      return VIE_EINVAL;
+    }
+    if (3 * b.ny * b.nz > 1152) { set_error("vie_plan_create: box cross-section too large (m > 1152)"); return VIE_EINVAL; }
+  }
+  VIE_TRY(fft_get(d.L, &P->fL));
+  VIE_TRY(fft_get(d.Py, &P->fPy));
+  VIE_TRY(fft_get(d.Pz, &P->fPz));
+  VIE_TRY(build_spectra(P.get()));
+  VIE_TRY(matvec_alloc(P.get()));
+  *out = P.release();
+  return VIE_OK;
+}
+
+void vie_plan_destroy(vie_plan_t P) {
+  if (!P) return;
+  {
+    StreamScope scope(P->st);
+    cudaStreamSynchronize(P->st);
+    krylov_free(P);
+    precond_free(P);
+    delete P;
+  }
+  cudaGetLastError();
+}
+
+vie_status vie_set_permittivity(vie_plan_t P, const void* eps) {
+  if (!P || !eps) { set_error("vie_set_permittivity: NULL argument"); return VIE_EINVAL; }
+  StreamScope scope(P->st);
+  VIE_TRY(set_material(P, (const double2*)eps));
+  precond_free(P);
+  reset_graphs(P);
+  P->has_eps = true;
+  return VIE_OK;
+}
+
+vie_status vie_build_preconditioner(vie_plan_t P) {
+  if (!P) { set_error("vie_build_preconditioner: NULL plan"); return VIE_EINVAL; }
+  if (!P->has_eps) { set_error("vie_build_preconditioner: permittivity not set"); return VIE_ESTATE; }
+  StreamScope scope(P->st);
+  reset_graphs(P);
+  VIE_TRY(precond_build(P));
+  VIE_CUDA(cudaStreamSynchronize(P->st));
+  return VIE_OK;
+}
+
+vie_status vie_matvec(vie_plan_t P, const void* x, void* y, int precision) {
+  if (!P || !x || !y || x == y) { set_error("vie_matvec: bad arguments"); return VIE_EINVAL; }
+  if (!P->has_eps) { set_error("vie_matvec: permittivity not set"); return VIE_ESTATE; }
+  StreamScope scope(P->st);
+  const long long n3 = 3LL * P->nx * P->ny * P->nz;
+  if (precision == VIE_FP64) {
+    return matvec<double2>(P, (const double2*)x, (double2*)y, P->M128.as<double2>(), P->spec128.as<double2>(),
+                           P->T128.as<double2>(), P->S128.as<double2>(), P->st);
+  }
+  if (precision != VIE_MIXED) { set_error("vie_matvec: bad precision"); return VIE_EINVAL; }
+  VIE_TRY(narrow((const double2*)x, P->xin64.as<float2>(), n3, P->st));
+  VIE_TRY(matvec<float2>(P, P->xin64.as<float2>(), P->xout64.as<float2>(), P->M64.as<float2>(),
+                         P->spec64.as<float2>(), P->T64.as<float2>(), P->S64.as<float2>(), P->st));
+  return widen(P->xout64.as<float2>(), (double2*)y, n3, P->st);
+}
+
+vie_status vie_precond_apply(vie_plan_t P, const void* r, void* z, int precision) {
+  if (!P || !r || !z || r == z) { set_error("vie_precond_apply: bad arguments"); return VIE_EINVAL; }
+  if (!P->prec_built) { set_error("vie_precond_apply: preconditioner not built"); return VIE_ESTATE; }
+  StreamScope scope(P->st);
+  const long long n3 = 3LL * P->nx * P->ny * P->nz;
+  if (precision == VIE_FP64) return precond_apply<double2>(P, (const double2*)r, (double2*)z, P->st);
+  if (precision != VIE_MIXED) { set_error("vie_precond_apply: bad precision"); return VIE_EINVAL; }
+  VIE_TRY(narrow((const double2*)r, P->xin64.as<float2>(), n3, P->st));
+  VIE_TRY(precond_apply<float2>(P, P->xin64.as<float2>(), P->xout64.as<float2>(), P->st));
+  return widen(P->xout64.as<float2>(), (double2*)z, n3, P->st);
+}
+
+vie_status vie_solve(vie_plan_t P, const void* e_inc, void* w_out, vie_info* info) {
+  if (!P || !e_inc || !w_out) { set_error("vie_solve: NULL argument"); return VIE_EINVAL; }
+  StreamScope scope(P->st);
+  return solve(P, (const double2*)e_inc, (double2*)w_out, info);
+}
+
+vie_status vie_solve_host(vie_plan_t P, const void* eps_host, const void* e_inc_host, void* w_out_host,
+                          vie_info* info) {
+  if (!P || !eps_host || !e_inc_host || !w_out_host) { set_error("vie_solve_host: NULL argument"); return VIE_EINVAL; }
+  StreamScope scope(P->st);
+  const long long N = (long long)P->nx * P->ny * P->nz;
+  DevBuf eps, e, w;
+  VIE_TRY(eps.alloc(sizeof(double2) * N));
+  VIE_TRY(e.alloc(sizeof(double2) * 3 * N));
+  VIE_TRY(w.alloc(sizeof(double2) * 3 * N));
+  VIE_CUDA(cudaMemcpyAsync(eps.p, eps_host, sizeof(double2) * N, cudaMemcpyHostToDevice, P->st));
+  VIE_CUDA(cudaMemcpyAsync(e.p, e_inc_host, sizeof(double2) * 3 * N, cudaMemcpyHostToDevice, P->st));
+  VIE_TRY(vie_set_permittivity(P, eps.p));
+  const vie_status s = solve(P, e.as<double2>(), w.as<double2>(), info);
+  if (s < 0) return s;
+  VIE_CUDA(cudaMemcpyAsync(w_out_host, w.p, sizeof(double2) * 3 * N, cudaMemcpyDeviceToHost, P->st));
+  VIE_CUDA(cudaStreamSynchronize(P->st));
+  return s;
+}
+
+vie_status vie_solve_batch(vie_plan_t* plans, int n, const void* const* e_inc, void* const* w_out, vie_info* info) {
+  if (n < 0 || (n > 0 && (!plans || !e_inc || !w_out))) { set_error("vie_solve_batch: bad arguments"); return VIE_EINVAL; }
+  std::vector<vie_status> st(n, VIE_OK);
+  std::vector<std::string> errs(n);
+  std::vector<std::thread> th;
+  for (int i = 0; i < n; ++i) {
+    th.emplace_back([&, i] {
+      cudaSetDevice(plans[i]->device);
+      st[i] = vie_solve(plans[i], e_inc[i], w_out[i], info ? info + i : nullptr);
+      if (st[i] < 0) errs[i] = vie_last_error();
+    });
+  }
+  for (auto& t : th) t.join();
+  vie_status worst = VIE_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st[i] < 0 && (worst >= 0 || st[i] < worst)) { worst = st[i]; set_error("%s", errs[i].c_str()); }
+    else if (worst == VIE_OK && st[i] > 0) worst = st[i];
+  }
+  return worst;
+}
+
+size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
+  vie_opts o;
+  if (opts) o = *opts; else vie_default_opts(&o);
+  const double N = (double)nx * ny * nz;
+  const double L = 2.0 * fft_next_smooth(nx), Py = 2.0 * fft_next_smooth(ny), Pz = 2.0 * fft_next_smooth(nz);
+  const double spec = 6.0 * (L / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1) * (16 + 8);
+  const double full = L * Py * Pz * 16;                  // spectra assembly scratch
+  const double T = 3.0 * Pz * Py * nx * (16 + 8);
+  const double Sx = (3.0 * L * 16 > 200 * 1024) ? 3.0 * Pz * Py * L * (16 + 8) : 0;
+  const double vec = N * 3 * (16 * 6 + 8 * 8) + N * 24;
+  const int R = o.restart;
+  const double basis = N * 3 * (R + 1) * (o.precision == VIE_MIXED ? 8 : 16);
+  double prec = 0;
+  if (o.precond == VIE_PREC_CIRCULANT) {
+    std::vector<vie_box> bs;
+    if (o.nboxes > 0 && o.boxes) bs.assign(o.boxes, o.boxes + o.nboxes);
+    else bs.push_back(vie_box{0, 0, 0, nx, ny, nz});
+    for (const vie_box& b : bs) {
+      const double m = 3.0 * b.ny * b.nz;
+      const double half = b.nx / 2 + 1;
+      const double kept = o.reduce_tol > 0 ? std::min(half, 0.3 * half + 2) : half;
+      const double lam = 6.0 * (2 * b.ny - 1) * (2 * b.nz - 1) * b.nx * 16 * 2;
+      const double blocks = kept * m * m * (16 + (o.precision == VIE_MIXED ? 8 : 16));
+      prec += lam + blocks + 4.0 * b.nx * m * 16;
+    }
+  }
+  return (size_t)(spec + full + T + Sx + vec + basis + prec + 64.0 * 1024 * 1024);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// continuous-batching server
+// ---------------------------------------------------------------------------
+struct SrvReq {
+  int64_t id;
+  int nx, ny, nz;
+  double h, k0, eps_bg;
+  vie_opts opts;
+  std::vector<vie_box> boxes;
+  std::vector<double2> eps, e;
+  void* w_out;
+  size_t est;
+  vie_status status = VIE_PENDING;
+  vie_info info{};
+  std::string err;
+};
+
+struct vie_server_s {
+  size_t budget = 0;
+  int max_inflight = 1;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SrvReq*> queue;
+  std::map<int64_t, std::unique_ptr<SrvReq>> all;
+  size_t reserved = 0;
+  int running = 0;
+  int64_t next_id = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+};
+
+static void server_run_one(vie_server_s* S, SrvReq* R, cudaStream_t st) {
+  vie_plan_t plan = nullptr;
+  vie_status s = vie_plan_create(R->nx, R->ny, R->nz, R->h, R->k0, R->eps_bg, &R->opts, st, &plan);
+  if (s >= 0) s = vie_solve_host(plan, R->eps.data(), R->e.data(), R->w_out, &R->info);
+  if (s < 0) R->err = vie_last_error();
+  vie_plan_destroy(plan);
+  R->status = s;
+}
+
+static void server_worker(vie_server_s* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (;;) {
+    SrvReq* R = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      // admit the oldest request once its footprint fits the budget
+      S->cv_work.wait(lk, [&] {
+        return S->stop || (!S->queue.empty() && S->reserved + S->queue.front()->est <= S->budget);
+      });
+      if (S->stop && S->queue.empty()) break;
+      if (S->stop) break;
+      R = S->queue.front();
+      S->queue.pop_front();
+      S->reserved += R->est;
+      S->running += 1;
+    }
+    server_run_one(S, R, st);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->reserved -= R->est;
+      S->running -= 1;
+      R->eps.clear(); R->eps.shrink_to_fit();
+      R->e.clear(); R->e.shrink_to_fit();
+    }
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+extern "C" {
+
+vie_status vie_server_create(size_t budget_bytes, int max_inflight, vie_server_t* out) {
+  if (!out || budget_bytes == 0 || max_inflight < 1 || max_inflight > 64) {
+    set_error("vie_server_create: bad arguments");
+    return VIE_EINVAL;
+  }
+  init_pool();
+  vie_server_s* S = new vie_server_s();
+  S->budget = budget_bytes;
+  S->max_inflight = max_inflight;
+  cudaGetDevice(&S->device);
+  for (int i = 0; i < max_inflight; ++i) S->workers.emplace_back(server_worker, S);
+  *out = S;
+  return VIE_OK;
+}
+
+vie_status vie_server_submit(vie_server_t S, int nx, int ny, int nz, double h, double k0, double eps_bg,
+                             const vie_opts* opts, const void* eps_host, const void* e_inc_host, void* w_out_host,
+                             int64_t* ticket) {
+  if (!S || !eps_host || !e_inc_host || !w_out_host || !ticket || nx < 1 || ny < 1 || nz < 1) {
+    set_error("vie_server_submit: bad arguments");
+    return VIE_EINVAL;
+  }
+  std::unique_ptr<SrvReq> R(new SrvReq());
+  R->nx = nx; R->ny = ny; R->nz = nz; R->h = h; R->k0 = k0; R->eps_bg = eps_bg;
+  if (opts) R->opts = *opts; else vie_default_opts(&R->opts);
+  if (R->opts.nboxes > 0 && R->opts.boxes) R->boxes.assign(R->opts.boxes, R->opts.boxes + R->opts.nboxes);
+  R->opts.boxes = R->boxes.empty() ? nullptr : R->boxes.data();
+  R->opts.nboxes = (int)R->boxes.size();
+  R->est = vie_estimate_bytes(nx, ny, nz, &R->opts);
+  const size_t N = (size_t)nx * ny * nz;
+  R->w_out = w_out_host;
+  std::lock_guard<std::mutex> lk(S->mu);
+  R->id = S->next_id++;
+  *ticket = R->id;
+  if (R->est > S->budget) {
+    R->status = VIE_EREJECTED;
+    R->err = "request footprint exceeds the server budget";
+    S->all[R->id] = std::move(R);
+    set_error("vie_server_submit: request footprint exceeds the server budget");
+    return VIE_EREJECTED;
+  }
+  R->eps.assign((const double2*)eps_host, (const double2*)eps_host + N);
+  R->e.assign((const double2*)e_inc_host, (const double2*)e_inc_host + 3 * N);
+  S->queue.push_back(R.get());
+  S->all[R->id] = std::move(R);
+  S->cv_work.notify_all();
+  return VIE_OK;
+}
+
+vie_status vie_server_poll(vie_server_t S, int64_t ticket, vie_info* info) {
+  if (!S) { set_error("vie_server_poll: NULL server"); return VIE_EINVAL; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) { set_error("vie_server_poll: unknown ticket"); return VIE_EINVAL; }
+  SrvReq* R = it->second.get();
+  if (R->status == VIE_PENDING) return VIE_PENDING;
+  if (info) *info = R->info;
+  if (R->status < 0) set_error("%s", R->err.c_str());
+  return R->status;
+}
+
+vie_status vie_server_drain(vie_server_t S, double timeout_ms) {
+  if (!S) { set_error("vie_server_drain: NULL server"); return VIE_EINVAL; }
+  std::unique_lock<std::mutex> lk(S->mu);
+  const auto pred = [&] { return S->queue.empty() && S->running == 0; };
+  if (timeout_ms < 0) { S->cv_done.wait(lk, pred); return VIE_OK; }
+  if (!S->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred)) {
+    set_error("vie_server_drain: timed out");
+    return VIE_ETIMEOUT;
+  }
+  return VIE_OK;
+}
+
+size_t vie_server_reserved_bytes(vie_server_t S) {
+  if (!S) return 0;
+  std::lock_guard<std::mutex> lk(S->mu);
+  return S->reserved;
+}
+
+void vie_server_destroy(vie_server_t S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    for (SrvReq* R : S->queue) { R->status = VIE_EREJECTED; R->err = "server destroyed"; }
+    S->queue.clear();
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// Batched line FFTs through shared memory, with Bluestein's chirp-z
+// decomposition for lengths that are not 7-smooth.
+#include <math.h>
+#include <stdarg.h>
+
+#include <atomic>
+#include <complex>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "fft.cuh"
+
+namespace vie {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+long long launches_total() { return g_launches.load(); }
+
+bool fft_smooth(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int fft_next_smooth(int n) {
+  if (n < 1) n = 1;
+  while (!fft_smooth(n)) ++n;
+  return n;
+}
+
+static int next_pow2(int n) {
+  int m = 1;
+  while (m < n) m <<= 1;
+  return m;
+}
+
+// radix sequence: 8s, then one 4 or 2, then 3s, 5s, 7s
+static bool factorize(int n, FftPlanDev& p) {
+  p.n = n;
+  p.npass = 0;
+  int m = n, a = 0;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (a >= 3) { p.radix[p.npass++] = 8; a -= 3; }
+  if (a == 2) p.radix[p.npass++] = 4;
+  if (a == 1) p.radix[p.npass++] = 2;
+  for (int r : {3, 5, 7})
+    while (m % r == 0) { p.radix[p.npass++] = r; m /= r; if (p.npass >= FFT_MAX_PASSES) return false; }
+  return m == 1 && p.npass <= FFT_MAX_PASSES;
+}
+
+template <class C>
+static vie_status upload(const std::vector<std::complex<double>>& v, C** out) {
+  std::vector<C> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = cmake<C>((typename real_of<C>::type)v[i].real(),
+                                                        (typename real_of<C>::type)v[i].imag());
+  VIE_CUDA(cudaMalloc((void**)out, sizeof(C) * (v.size() ? v.size() : 1)));
+  VIE_CUDA(cudaMemcpy(*out, h.data(), sizeof(C) * v.size(), cudaMemcpyHostToDevice));
+  return VIE_OK;
+}
+
+static vie_status make_plan(int n, FftPlanDev& p64, FftPlanDev& p32) {
+  if (!factorize(n, p64)) { set_error("fft: %d is not 7-smooth", n); return VIE_EINVAL; }
+  p32 = p64;
+  std::vector<std::complex<double>> tw(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)n;
+    tw[k] = std::complex<double>(cos(a), sin(a));
+  }
+  double2* t64; float2* t32;
+  VIE_TRY(upload(tw, &t64));
+  VIE_TRY(upload(tw, &t32));
+  p64.tw = t64;
+  p32.tw = t32;
+  return VIE_OK;
+}
+
+// host radix-2 FFT (sign -1), used once per Bluestein length for the chirp
+// spectrum
+static void host_fft_pow2(std::vector<std::complex<double>>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    for (size_t i = 0; i < n; i += len) {
+      for (size_t k = 0; k < len / 2; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)len;
+        const std::complex<double> w(cos(ang), sin(ang));
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+static std::mutex g_fft_mu;
+static std::map<int, std::unique_ptr<FftLen>>* g_fft_cache = nullptr;
+
+vie_status fft_get(int n, const FftLen** out) {
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  if (!g_fft_cache) g_fft_cache = new std::map<int, std::unique_ptr<FftLen>>();
+  auto it = g_fft_cache->find(n);
+  if (it != g_fft_cache->end()) { *out = it->second.get(); return VIE_OK; }
+  if (n < 1) { set_error("fft: bad length %d", n); return VIE_EINVAL; }
+  std::unique_ptr<FftLen> f(new FftLen());
+  f->n = n;
+  if (fft_smooth(n)) {
+    VIE_TRY(make_plan(n, f->pn64, f->pn32));
+  } else {
+    f->bluestein = true;
+    f->M = next_pow2(2 * n - 1);
+    const int M = f->M;
+    VIE_TRY(make_plan(M, f->pm64, f->pm32));
+    std::vector<std::complex<double>> b(n);
+    for (int k = 0; k < n; ++k) {
+      const long long e = ((long long)k * k) % (2LL * n);
+      const double a = M_PI * (double)e / (double)n;
+      b[k] = std::complex<double>(cos(a), sin(a));
+    }
+    std::vector<std::complex<double>> cf(M, 0.0), ci(M, 0.0);
+    for (int j = 0; j < n; ++j) {
+      cf[j] = b[j];
+      ci[j] = std::conj(b[j]);
+      if (j > 0) { cf[M - j] = b[j]; ci[M - j] = std::conj(b[j]); }
+    }
+    host_fft_pow2(cf);
+    host_fft_pow2(ci);
+    for (int j = 0; j < M; ++j) { cf[j] /= (double)M; ci[j] /= (double)M; }
+    VIE_TRY(upload(b, &f->chirp64));
+    VIE_TRY(upload(b, &f->chirp32));
+    VIE_TRY(upload(cf, &f->hatf64));
+    VIE_TRY(upload(cf, &f->hatf32));
+    VIE_TRY(upload(ci, &f->hati64));
+    VIE_TRY(upload(ci, &f->hati32));
+  }
+  *out = f.get();
+  (*g_fft_cache)[n] = std::move(f);
+  return VIE_OK;
+}
+
+template <class C> static const FftPlanDev& plan_n(const FftLen& f);
+template <> const FftPlanDev& plan_n<double2>(const FftLen& f) { return f.bluestein ? f.pm64 : f.pn64; }
+template <> const FftPlanDev& plan_n<float2>(const FftLen& f) { return f.bluestein ? f.pm32 : f.pn32; }
+
+template <class C> int fft_max_len() { return (int)((200 * 1024) / sizeof(C)) - 64; }
+template int fft_max_len<float2>();
+template int fft_max_len<double2>();
+
+// pre/post modes: 0 none, 1 multiply, 2 multiply by conjugate
+template <class C, int MAXE>
+__global__ void __launch_bounds__(1024) k_fft_lines(const C* __restrict__ in, C* __restrict__ out,
+                                                    LineDesc d, FftPlanDev p, int sign, int lpc,
+                                                    const C* __restrict__ pre, int pre_mode,
+                                                    const C* __restrict__ post, int post_mode,
+                                                    const C* __restrict__ post2, int post2_mode,
+                                                    double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  using T = typename real_of<C>::type;
+  const int n = p.n;
+  const int pitch = n + 1;
+  const int l0 = blockIdx.x * lpc;
+  const int nl = min(lpc, d.nlines - l0);
+  const int E = nl * n;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    int li, i;
+    if (d.ies == 1) { li = e / n; i = e - li * n; } else { i = e / nl; li = e - i * nl; }
+    const int l = l0 + li;
+    C v = czero<C>();
+    if (i < d.n_in) {
+      const long long off = line_in_off(d, l) + (long long)i * d.ies;
+      v = in[off];
+      if (pre_mode) { C w = pre[i]; if (pre_mode == 2) w.y = -w.y; v = cmul(v, w); }
+    }
+    s[li * pitch + i] = v;
+  }
+  __syncthreads();
+  SmemLines L{nl, nl, pitch, 0, 1, 0};
+  fft_smem<MAXE>(s, p, L, sign);
+  const T sc = (T)scale;
+  const int Eo = nl * d.n_out;
+  for (int e = threadIdx.x; e < Eo; e += blockDim.x) {
+    int li, f;
+    if (d.oes == 1) { li = e / d.n_out; f = e - li * d.n_out; } else { f = e / nl; li = e - f * nl; }
+    const int l = l0 + li;
+    C v = s[li * pitch + f];
+    if (post_mode) { C w = post[f]; if (post_mode == 2) w.y = -w.y; v = cmul(v, w); }
+    if (post2_mode) { C w = post2[f]; if (post2_mode == 2) w.y = -w.y; v = cmul(v, w); }
+    const long long off = line_out_off(d, l) + (long long)f * d.oes;
+    out[off] = cscale(v, sc);
+  }
+}
+
+template <class C>
+static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const FftPlanDev& p, int sign,
+                               const C* pre, int pre_mode, const C* post, int post_mode,
+                               const C* post2, int post2_mode, double scale, cudaStream_t st) {
+  const int n = p.n;
+  if (n > fft_max_len<C>()) { set_error("fft: line length %d too long for shared memory", n); return VIE_EINVAL; }
+  if (d.nlines <= 0) return VIE_OK;
+  const size_t line_bytes = (size_t)(n + 1) * sizeof(C);
+  const size_t budget = 48 * 1024;
+  int lpc = (int)(budget / line_bytes);
+  if (lpc < 1) lpc = 1;
+  if (lpc > d.nlines) lpc = d.nlines;
+  if (lpc > 64) lpc = 64;
+  const long long E = (long long)lpc * n;
+  int threads = 128;
+  while (threads < 1024 && E > 8LL * threads) threads *= 2;
+  const int per = (int)((E + threads - 1) / threads);
+  const size_t smem = (size_t)lpc * line_bytes;
+  const int grid = (d.nlines + lpc - 1) / lpc;
+#define VIE_LAUNCH_LINES(ME)                                                                      \
+  {                                                                                               \
+    auto kern = k_fft_lines<C, ME>;                                                               \
+    if (smem > 48 * 1024)                                                                         \
+      VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode,  \
+                                      post2, post2_mode, scale);                                 \
+  }
+  if (per <= 4) VIE_LAUNCH_LINES(4)
+  else if (per <= 8) VIE_LAUNCH_LINES(8)
+  else if (per <= 16) VIE_LAUNCH_LINES(16)
+  else if (per <= 32) VIE_LAUNCH_LINES(32)
+  else { set_error("fft: tile of %lld elements too large", E); return VIE_EINVAL; }
+#undef VIE_LAUNCH_LINES
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+template <class C> struct Tabs;
+template <> struct Tabs<double2> {
+  static const double2* chirp(const FftLen& f) { return f.chirp64; }
+  static const double2* hatf(const FftLen& f) { return f.hatf64; }
+  static const double2* hati(const FftLen& f) { return f.hati64; }
+};
+template <> struct Tabs<float2> {
+  static const float2* chirp(const FftLen& f) { return f.chirp32; }
+  static const float2* hatf(const FftLen& f) { return f.hatf32; }
+  static const float2* hati(const FftLen& f) { return f.hati32; }
+};
+
+template <class C>
+vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, int sign, double scale,
+                     C* tmp, cudaStream_t st) {
+  if (d.n_in > f.n || d.n_out > f.n) { set_error("fft: line desc exceeds length"); return VIE_EINVAL; }
+  if (!f.bluestein) {
+    return launch_lines<C>(in, out, d, plan_n<C>(f), sign, nullptr, 0, nullptr, 0, nullptr, 0, scale, st);
+  }
+  if (!tmp) { set_error("fft: Bluestein length %d needs a scratch buffer", f.n); return VIE_EINVAL; }
+  // step 1: a_k = x_k * conj(b_k) (forward) or x_k * b_k (inverse), FFT_M, times chirp spectrum
+  LineDesc d1 = d;
+  d1.os1 = f.M; d1.os2 = (long long)f.M * d.nl1; d1.os3 = (long long)f.M * d.nl1 * d.nl2;
+  d1.oes = 1; d1.n_out = f.M;
+  const C* chirp = Tabs<C>::chirp(f);
+  const C* hat = sign < 0 ? Tabs<C>::hatf(f) : Tabs<C>::hati(f);
+  VIE_TRY(launch_lines<C>(in, tmp, d1, plan_n<C>(f), -1, chirp, sign < 0 ? 2 : 1, hat, 1, nullptr, 0, 1.0, st));
+  // step 2: inverse FFT_M (the 1/M is in the chirp spectrum), times conj(b_f) or b_f
+  LineDesc d2 = d;
+  d2.n_in = f.M; d2.is1 = f.M; d2.is2 = (long long)f.M * d.nl1; d2.is3 = (long long)f.M * d.nl1 * d.nl2;
+  d2.ies = 1;
+  return launch_lines<C>(tmp, out, d2, plan_n<C>(f), +1, nullptr, 0, chirp, sign < 0 ? 2 : 1,
+                         nullptr, 0, scale, st);
+}
+
+template vie_status fft_lines<double2>(const double2*, double2*, const LineDesc&, const FftLen&, int,
+                                       double, double2*, cudaStream_t);
+template vie_status fft_lines<float2>(const float2*, float2*, const LineDesc&, const FftLen&, int,
+                                      double, float2*, cudaStream_t);
+
+}  // namespace vie

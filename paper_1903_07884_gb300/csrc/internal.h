@@ -1,0 +1,121 @@
+// Internal declarations shared by the libvie translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <vector>
+
+#include "fft.cuh"
+#include "vie_common.cuh"
+
+namespace vie {
+
+// Device allocation owned by a plan (freed on destruction).  Allocations are
+// stream-ordered on the stream of the API call that makes them.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release();
+  vie_status alloc(size_t n);
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Matvec geometry passed to kernels.
+struct MvDims {
+  int nx, ny, nz;       // grid
+  int L, Py, Pz;        // circulant embedding lengths
+  int Lh, Pyh, Pzh;     // stored (non-negative) spectral octant: L/2+1, ...
+};
+
+// One partition box of the preconditioner with its factorised blocks.
+struct BoxPrec {
+  vie_box b{};
+  int m = 0;                 // 3 * ny * nz
+  int n = 0;                 // nx of the box (circulant length)
+  int nhalf = 0;             // frequencies 0..nhalf-1 carry stored blocks (S1 symmetry)
+  int rep = 0;               // representative frequency ceil(n/2) - 1
+  int nblk = 0;              // stored blocks: kept f <= n/2 plus the representative
+  int nkept = 0;             // kept frequencies (full range 0..n-1)
+  int ndisc = 0;             // discarded frequencies (use the representative)
+  DevBuf Mt;                 // double2 [nz][ny] homogenised M~
+  DevBuf lam;                // double2 [6][2nz-1][2ny-1][n] Chan eigenvalues
+  DevBuf vhat;               // double  [n]
+  DevBuf fmap;               // int [n]: block slot for f (S1 folded), -1 -> representative
+  DevBuf fsgn;               // int [n]: 1 if f uses S D S (f > n/2)
+  DevBuf disc;               // int [ndisc]: discarded frequencies
+  DevBuf blkf;               // int [nblk]: frequency of each stored block
+  DevBuf inv64;              // float2  [nblk][m][m] row-major D_f^{-1} (mixed path)
+  DevBuf inv128;             // double2 [nblk][m][m] row-major D_f^{-1} (FP64 path)
+  DevBuf rhat64, rhat128;    // [n][m] frequency-major work vectors
+  DevBuf zhat64, zhat128;
+  DevBuf tmp64, tmp128;      // Bluestein scratch [m][M] (non-smooth n only)
+  const FftLen* fx = nullptr;
+};
+
+struct Krylov;   // krylov.cu
+
+}  // namespace vie
+
+struct vie_plan_s {
+  int nx = 0, ny = 0, nz = 0;
+  double h = 0, k0 = 0, eps_bg = 1, kb = 0;
+  vie_opts opts{};
+  std::vector<vie_box> boxes;
+  cudaStream_t st = nullptr;
+  int device = 0;
+
+  vie::MvDims d{};
+  const vie::FftLen *fL = nullptr, *fPy = nullptr, *fPz = nullptr;
+  bool fused_x128 = true, fused_x64 = true;   // fused x-pass fits shared memory
+  vie::DevBuf spec128, spec64;         // [6][Pzh][Pyh][Lh] scaled generator spectra
+  vie::DevBuf M128, M64;               // [nz][ny][nx] material M
+  vie::DevBuf T128, T64;               // [3][Pz][Py][nx] matvec intermediate
+  vie::DevBuf S128, S64;               // [3][Pz][Py][L] full x-spectrum (unfused path only)
+  vie::DevBuf xin64, xout64;           // c64 staging for vie_matvec / precond (mixed)
+  bool has_eps = false;
+  bool prec_built = false;
+  std::vector<std::unique_ptr<vie::BoxPrec>> bp;
+  size_t precond_bytes = 0;
+  double kept_fraction = 1.0;
+  float t_setup_ms = 0;
+  std::unique_ptr<vie::Krylov> kry;
+  size_t bytes_allocated = 0;
+  vie_plan_s();
+  ~vie_plan_s();
+};
+
+namespace vie {
+
+long long launches_total();
+
+// greens.cu
+vie_status build_spectra(vie_plan_s* P);
+vie_status set_material(vie_plan_s* P, const double2* eps);
+
+// matvec.cu
+template <class C>
+vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C* T, C* S, cudaStream_t st);
+vie_status matvec_alloc(vie_plan_s* P);
+
+// precond.cu
+vie_status precond_build(vie_plan_s* P);
+template <class C>
+vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st);
+void precond_free(vie_plan_s* P);
+
+// krylov.cu
+vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w, vie_info* info);
+void krylov_free(vie_plan_s* P);
+void reset_graphs(vie_plan_s* P);
+
+// conversions
+vie_status widen(const float2* a, double2* b, long long n, cudaStream_t st);
+vie_status narrow(const double2* a, float2* b, long long n, cudaStream_t st);
+
+}  // namespace vie

@@ -1,0 +1,693 @@
+// Right-preconditioned restarted GMRES (the Krylov solver of Sec. 1 / Sec. 3)
+// and FP64 iterative refinement around a complex-FP32 inner GMRES.
+//
+// One Arnoldi step with classical Gram-Schmidt and one re-orthogonalisation
+// (CGS2): z = P^-1 v_j, w = A z, h = V^H w, w -= V h (twice), h_{j+1,j} =
+// ||w||, v_{j+1} = w / h_{j+1,j}.  The Hessenberg column is reduced by complex
+// Givens rotations on the device; |g_{j+1}| is the residual estimate.  All
+// reductions are two-stage and fixed-order, so results are bitwise
+// reproducible for a given size and launch shape.
+//
+// The iteration index j, the rotations and the stop flag live in device
+// memory; one captured CUDA graph replays a whole Arnoldi step, and the host
+// only polls the stop flag between chunks of steps.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "internal.h"
+
+namespace vie {
+
+constexpr int RMAX = 128;      // largest supported restart length
+constexpr int NPART = 304;     // CTAs of the reduction kernels (2 per SM)
+constexpr int RED_THREADS = 256;
+
+struct GmresDev {
+  double2 H[(RMAX + 1) * RMAX];   // column j at H[j*(RMAX+1) + i], after rotations
+  double cs[RMAX];
+  double2 sn[RMAX];
+  double2 g[RMAX + 1];
+  double2 y[RMAX];
+  double2 hc[RMAX + 1];           // coefficients of the current projection step
+  double2 hsum[RMAX + 1];         // accumulated column (both CGS passes)
+  double beta;                    // norm of the cycle's starting residual
+  double tol_abs;                 // stop when |g_{j+1}| <= tol_abs
+  double hnext;                   // h_{j+1,j}
+  double resest;                  // |g_{j+1}|
+  int j;                          // current column
+  int k;                          // columns in the finished cycle
+  int done;                       // 1: cycle finished (converged, full, or breakdown)
+  int restart;
+  int iters;                      // total Arnoldi steps of this state
+  int pad[3];
+};
+
+struct Krylov {
+  int restart = 0;
+  long long n3 = 0;
+  DevBuf V64, V128;               // (restart + 1) * n3 basis
+  DevBuf u64, u128, z64, z128, w64, w128;
+  DevBuf partial;                 // double2 [NPART][RMAX + 1]
+  DevBuf state;                   // GmresDev
+  DevBuf x128, r128, b128, d64, rhs64, r64, t128;
+  DevBuf scal;                    // double [8]: norms
+  int* hflag = nullptr;           // pinned host mirror: done, iters
+  cudaGraphExec_t g64 = nullptr, g128 = nullptr;
+  int step_launches = 0;
+  cudaEvent_t ev = nullptr;
+  cudaStream_t cap = nullptr;     // private stream for graph capture
+  ~Krylov() {
+    if (cap) cudaStreamDestroy(cap);
+    if (g64) cudaGraphExecDestroy(g64);
+    if (g128) cudaGraphExecDestroy(g128);
+    if (ev) cudaEventDestroy(ev);
+    if (hflag) cudaFreeHost(hflag);
+  }
+};
+
+void krylov_free(vie_plan_s* P) { P->kry.reset(); }
+
+}  // namespace vie
+
+vie_plan_s::vie_plan_s() = default;
+vie_plan_s::~vie_plan_s() = default;
+
+namespace vie {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <class C> struct Acc;   // per-thread accumulator type
+template <> struct Acc<float2> { using T = float; };
+template <> struct Acc<double2> { using T = double; };
+
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double2 t = make_double2(0, 0);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t.x += sh[w].x; t.y += sh[w].y; }
+  return t;   // valid in thread 0
+}
+
+// partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j
+template <class C>
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
+                                                             long long n3, const GmresDev* __restrict__ s,
+                                                             double2* __restrict__ partial) {
+  __shared__ double2 sh[32];
+  if (s->done) return;
+  const int j = s->j;
+  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
+  using T = typename Acc<C>::T;
+  for (int i = 0; i <= j; ++i) {
+    const C* Vi = V + (long long)i * n3;
+    T ar = 0, ai = 0;
+    for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+      const C v = Vi[e], x = w[e];
+      ar += v.x * x.x + v.y * x.y;
+      ai += v.x * x.y - v.y * x.x;
+    }
+    const double2 t = block_sum2(make_double2(ar, ai), sh);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1) + i] = t;
+  }
+}
+
+// hc[i] = sum_b partial[b][i]; mode 0: hsum = hc, mode 1: hsum += hc
+__global__ void k_reduce_h(const double2* __restrict__ partial, GmresDev* __restrict__ s, int nparts, int mode) {
+  if (s->done) return;
+  const int j = s->j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    double2 t = make_double2(0, 0);
+    for (int b = 0; b < nparts; ++b) {
+      const double2 p = partial[(long long)b * (RMAX + 1) + i];
+      t.x += p.x;
+      t.y += p.y;
+    }
+    s->hc[i] = t;
+    if (mode == 0) s->hsum[i] = t;
+    else { s->hsum[i].x += t.x; s->hsum[i].y += t.y; }
+  }
+}
+
+// w -= sum_i hc[i] V_i ; optionally partial[b][0] = ||w||^2 over the chunk
+template <class C>
+__global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V, C* __restrict__ w, long long n3,
+                                                        const GmresDev* __restrict__ s, double2* __restrict__ partial,
+                                                        int want_norm) {
+  __shared__ double2 sh[32];
+  __shared__ C hcs[RMAX + 1];
+  if (s->done) return;
+  const int j = s->j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hcs[i] = cconv<C>(s->hc[i]);
+  __syncthreads();
+  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
+  using T = typename Acc<C>::T;
+  T nrm = 0;
+  for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+    C x = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const C v = V[(long long)i * n3 + e];
+      const C h = hcs[i];
+      x.x -= h.x * v.x - h.y * v.y;
+      x.y -= h.x * v.y + h.y * v.x;
+    }
+    w[e] = x;
+    nrm += x.x * x.x + x.y * x.y;
+  }
+  if (want_norm) {
+    const double2 t = block_sum2(make_double2(nrm, 0), sh);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1)] = t;
+  }
+}
+
+// Hessenberg column, rotations, residual estimate, stop test
+__global__ void k_givens(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts) {
+  if (threadIdx.x != 0 || s->done) return;
+  const int j = s->j;
+  double nn = 0;
+  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
+  const double hn = sqrt(nn);
+  double2* col = s->H + (long long)j * (RMAX + 1);
+  for (int i = 0; i <= j; ++i) col[i] = s->hsum[i];
+  col[j + 1] = make_double2(hn, 0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = col[i], b = col[i + 1];
+    const double c = s->cs[i];
+    const double2 sn = s->sn[i];
+    // [c s; -conj(s) c] [a; b]
+    col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
+    col[i + 1] = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
+  }
+  const double2 a = col[j];
+  const double b = hn;   // real, >= 0
+  double c;
+  double2 sn;
+  const double aa = sqrt(a.x * a.x + a.y * a.y);
+  if (b == 0.0) { c = 1.0; sn = make_double2(0, 0); }
+  else if (aa == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
+  else {
+    const double r = hypot(aa, b);
+    c = aa / r;
+    // s = a conj(b) / (|a| r), b real
+    sn = make_double2(a.x * b / (aa * r), a.y * b / (aa * r));
+  }
+  s->cs[j] = c;
+  s->sn[j] = sn;
+  col[j] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
+  col[j + 1] = make_double2(0, 0);
+  const double2 gj = s->g[j];
+  // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+  s->g[j + 1] = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
+  s->g[j] = make_double2(c * gj.x, c * gj.y);
+  const double res = sqrt(s->g[j + 1].x * s->g[j + 1].x + s->g[j + 1].y * s->g[j + 1].y);
+  s->resest = res;
+  s->hnext = hn;
+  s->iters += 1;
+  s->k = j + 1;
+  if (res <= s->tol_abs || j + 1 >= s->restart || hn == 0.0) s->done = 1;
+  else s->j = j + 1;
+}
+
+// V_{j} = w / h (j already advanced) and u = V_j
+template <class C>
+__global__ void k_scale_next(C* __restrict__ V, const C* __restrict__ w, C* __restrict__ u, long long n3,
+                             const GmresDev* __restrict__ s) {
+  if (s->done) return;
+  const int j = s->j;
+  using T = typename real_of<C>::type;
+  const T inv = (T)(1.0 / s->hnext);
+  C* Vj = V + (long long)j * n3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    const C v = cscale(w[e], inv);
+    Vj[e] = v;
+    u[e] = v;
+  }
+}
+
+// cycle start: beta = ||r||, V_0 = u = r / beta, g = beta e_1
+template <class C>
+__global__ void k_norm_partial(const C* __restrict__ r, long long n3, double2* __restrict__ partial) {
+  __shared__ double2 sh[32];
+  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
+  double nrm = 0;   // FP64 per thread: called once per cycle
+  for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nrm += (double)r[e].x * r[e].x + (double)r[e].y * r[e].y;
+  const double2 t = block_sum2(make_double2(nrm, 0), sh);
+  if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1)] = t;
+}
+
+__global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts, double tol_abs,
+                             int restart) {
+  if (threadIdx.x != 0) return;
+  double nn = 0;
+  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
+  const double beta = sqrt(nn);
+  s->beta = beta;
+  s->tol_abs = tol_abs;
+  s->restart = restart;
+  s->j = 0;
+  s->k = 0;
+  s->resest = beta;
+  for (int i = 0; i <= restart; ++i) s->g[i] = make_double2(0, 0);
+  s->g[0] = make_double2(beta, 0);
+  s->done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
+}
+
+template <class C>
+__global__ void k_cycle_v0(const C* __restrict__ r, C* __restrict__ V, C* __restrict__ u, long long n3,
+                           const GmresDev* __restrict__ s) {
+  using T = typename real_of<C>::type;
+  const T inv = s->beta > 0 ? (T)(1.0 / s->beta) : (T)0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    const C v = cscale(r[e], inv);
+    V[e] = v;
+    u[e] = v;
+  }
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k)
+__global__ void k_solve_y(GmresDev* __restrict__ s) {
+  if (threadIdx.x != 0) return;
+  const int k = s->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 t = s->g[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 h = s->H[(long long)l * (RMAX + 1) + i];
+      const double2 y = s->y[l];
+      t.x -= h.x * y.x - h.y * y.y;
+      t.y -= h.x * y.y + h.y * y.x;
+    }
+    const double2 d = s->H[(long long)i * (RMAX + 1) + i];
+    const double2 id = cinv(d);
+    s->y[i] = cmul(t, id);
+  }
+}
+
+// u = sum_{i<k} y_i V_i
+template <class C>
+__global__ void k_combine(const C* __restrict__ V, C* __restrict__ u, long long n3, const GmresDev* __restrict__ s) {
+  __shared__ C ys[RMAX];
+  const int k = s->k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = cconv<C>(s->y[i]);
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    C acc = czero<C>();
+    for (int i = 0; i < k; ++i) cfma(acc, ys[i], V[(long long)i * n3 + e]);
+    u[e] = acc;
+  }
+}
+
+// x += scale * z   (x FP64, z any precision)
+template <class C>
+__global__ void k_axpy_to64(double2* __restrict__ x, const C* __restrict__ z, long long n3, const double* __restrict__ sc,
+                            int sidx) {
+  const double a = sc ? sc[sidx] : 1.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    x[e].x += a * (double)z[e].x;
+    x[e].y += a * (double)z[e].y;
+  }
+}
+
+// r = b - t (FP64)
+__global__ void k_sub(const double2* __restrict__ b, const double2* __restrict__ t, double2* __restrict__ r, long long n3) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+    r[e] = make_double2(b[e].x - t[e].x, b[e].y - t[e].y);
+}
+__global__ void k_sub64(const float2* __restrict__ b, const float2* __restrict__ t, float2* __restrict__ r, long long n3) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+    r[e] = make_float2(b[e].x - t[e].x, b[e].y - t[e].y);
+}
+
+// out[idx] = sqrt(sum partial)
+__global__ void k_norm_final(const double2* __restrict__ partial, int nparts, double* __restrict__ out, int idx) {
+  if (threadIdx.x != 0) return;
+  double nn = 0;
+  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
+  out[idx] = sqrt(nn);
+}
+
+// rhs64 = r / ||r||
+__global__ void k_narrow_scaled(const double2* __restrict__ r, float2* __restrict__ o, long long n3,
+                                const double* __restrict__ sc, int sidx) {
+  const double n = sc[sidx];
+  const double inv = n > 0 ? 1.0 / n : 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+    o[e] = make_float2((float)(r[e].x * inv), (float)(r[e].y * inv));
+}
+
+// b = M e_inc
+__global__ void k_rhs(const double2* __restrict__ M, const double2* __restrict__ e, double2* __restrict__ b, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * N; i += (long long)gridDim.x * blockDim.x)
+    b[i] = cmul(M[i % N], e[i]);
+}
+
+template <class C>
+__global__ void k_axpy_same(C* __restrict__ x, const C* __restrict__ z, long long n3) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+    x[e] = cadd(x[e], z[e]);
+}
+template <class C>
+__global__ void k_sub_same(const C* __restrict__ b, const C* __restrict__ t, C* __restrict__ r, long long n3) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+    r[e] = csub(b[e], t[e]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 8); }
+
+template <class C>
+static vie_status axpy_same(C* x, const C* z, long long n3, cudaStream_t st) {
+  k_axpy_same<C><<<grid_for(n3), 256, 0, st>>>(x, z, n3);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+template <class C>
+static vie_status sub_same(const C* b, const C* t, C* r, long long n3, cudaStream_t st) {
+  k_sub_same<C><<<grid_for(n3), 256, 0, st>>>(b, t, r, n3);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+template <class C> struct KB;
+template <> struct KB<float2> {
+  static float2* V(Krylov& K) { return K.V64.as<float2>(); }
+  static float2* u(Krylov& K) { return K.u64.as<float2>(); }
+  static float2* z(Krylov& K) { return K.z64.as<float2>(); }
+  static float2* w(Krylov& K) { return K.w64.as<float2>(); }
+  static cudaGraphExec_t& g(Krylov& K) { return K.g64; }
+  static const float2* M(vie_plan_s* P) { return P->M64.as<float2>(); }
+  static const float2* spec(vie_plan_s* P) { return P->spec64.as<float2>(); }
+  static float2* T(vie_plan_s* P) { return P->T64.as<float2>(); }
+  static float2* S(vie_plan_s* P) { return P->S64.as<float2>(); }
+};
+template <> struct KB<double2> {
+  static double2* V(Krylov& K) { return K.V128.as<double2>(); }
+  static double2* u(Krylov& K) { return K.u128.as<double2>(); }
+  static double2* z(Krylov& K) { return K.z128.as<double2>(); }
+  static double2* w(Krylov& K) { return K.w128.as<double2>(); }
+  static cudaGraphExec_t& g(Krylov& K) { return K.g128; }
+  static const double2* M(vie_plan_s* P) { return P->M128.as<double2>(); }
+  static const double2* spec(vie_plan_s* P) { return P->spec128.as<double2>(); }
+  static double2* T(vie_plan_s* P) { return P->T128.as<double2>(); }
+  static double2* S(vie_plan_s* P) { return P->S128.as<double2>(); }
+};
+
+template <class C>
+static vie_status op_A(vie_plan_s* P, const C* x, C* y) {
+  return matvec<C>(P, x, y, KB<C>::M(P), KB<C>::spec(P), KB<C>::T(P), KB<C>::S(P), P->st);
+}
+
+template <class C>
+static vie_status op_Pinv(vie_plan_s* P, const C* r, C* z) {
+  return precond_apply<C>(P, r, z, P->st);
+}
+
+static vie_status krylov_alloc(vie_plan_s* P, bool need64, bool need128) {
+  if (!P->kry) P->kry.reset(new Krylov());
+  Krylov& K = *P->kry;
+  const long long n3 = 3LL * P->nx * P->ny * P->nz;
+  const int R = P->opts.restart;
+  K.restart = R;
+  K.n3 = n3;
+  if (!K.state.p) {
+    VIE_TRY(K.state.alloc(sizeof(GmresDev)));
+    VIE_CUDA(cudaMemset(K.state.p, 0, sizeof(GmresDev)));
+    VIE_TRY(K.partial.alloc(sizeof(double2) * NPART * (RMAX + 1)));
+    VIE_TRY(K.scal.alloc(sizeof(double) * 8));
+    VIE_TRY(K.x128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.r128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.b128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.t128.alloc(sizeof(double2) * n3));
+    VIE_CUDA(cudaHostAlloc((void**)&K.hflag, sizeof(int) * 4, cudaHostAllocDefault));
+    VIE_CUDA(cudaEventCreateWithFlags(&K.ev, cudaEventDisableTiming));
+    VIE_CUDA(cudaStreamCreateWithFlags(&K.cap, cudaStreamNonBlocking));
+  }
+  if (need64 && !K.V64.p) {
+    VIE_TRY(K.V64.alloc(sizeof(float2) * n3 * (R + 1)));
+    VIE_TRY(K.u64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.z64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.w64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.d64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.rhs64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.r64.alloc(sizeof(float2) * n3));
+  }
+  if (need128 && !K.V128.p) {
+    VIE_TRY(K.V128.alloc(sizeof(double2) * n3 * (R + 1)));
+    VIE_TRY(K.u128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.z128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.w128.alloc(sizeof(double2) * n3));
+  }
+  return VIE_OK;
+}
+
+// kernels in one captured Arnoldi step (for launch accounting)
+static int step_kernels(vie_plan_s* P) {
+  Krylov& K = *P->kry;
+  return K.step_launches;
+}
+
+// enqueue one Arnoldi step (u holds v_j on entry and v_{j+1} on exit)
+template <class C>
+static vie_status enqueue_step(vie_plan_s* P) {
+  Krylov& K = *P->kry;
+  cudaStream_t st = P->st;
+  GmresDev* s = K.state.as<GmresDev>();
+  double2* part = K.partial.as<double2>();
+  C* V = KB<C>::V(K);
+  C* u = KB<C>::u(K);
+  C* z = KB<C>::z(K);
+  C* w = KB<C>::w(K);
+  const long long n3 = K.n3;
+  VIE_TRY(op_Pinv<C>(P, u, z));
+  VIE_TRY(op_A<C>(P, z, w));
+  for (int pass = 0; pass < 2; ++pass) {
+    k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part);
+    k_reduce_h<<<1, 128, 0, st>>>(part, s, NPART, pass);
+    k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1);
+    count_launch(3);
+  }
+  k_givens<<<1, 32, 0, st>>>(s, part, NPART);
+  k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s);
+  count_launch(2);
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+// Run GMRES cycles on A x = rhs (precision C) from x = 0, accumulating the
+// solution into x (C).  Stops when the true relative residual (rhs - A x,
+// precision C) is <= tol, or after max_iter steps.  Returns the steps used
+// through *iters and the last true relative residual through *relres.
+template <class C>
+static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol, int max_iter, int* iters,
+                        double* relres) {
+  Krylov& K = *P->kry;
+  cudaStream_t st = P->st;
+  GmresDev* s = K.state.as<GmresDev>();
+  double2* part = K.partial.as<double2>();
+  const long long n3 = K.n3;
+  C* V = KB<C>::V(K);
+  C* u = KB<C>::u(K);
+  C* z = KB<C>::z(K);
+  C* w = KB<C>::w(K);
+  double* scal = K.scal.as<double>();
+  // ||rhs||
+  k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rhs, n3, part);
+  k_norm_final<<<1, 32, 0, st>>>(part, NPART, scal, 0);
+  VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(C) * n3, st));
+  VIE_CUDA(cudaMemcpyAsync(rwork, rhs, sizeof(C) * n3, cudaMemcpyDeviceToDevice, st));
+  count_launch(2);
+  double hsc[2];
+  VIE_CUDA(cudaMemcpyAsync(hsc, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = hsc[0];
+  *iters = 0;
+  *relres = 0;
+  if (bnorm == 0.0) return VIE_OK;
+  cudaGraphExec_t& gexec = KB<C>::g(K);
+  int total = 0;
+  double rr = 1.0;
+  while (total < max_iter) {
+    // cycle start from the current residual rwork
+    k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rwork, n3, part);
+    k_cycle_init<<<1, 32, 0, st>>>(s, part, NPART, tol * bnorm, std::min(K.restart, max_iter - total));
+    k_cycle_v0<C><<<grid_for(n3), 256, 0, st>>>(rwork, V, u, n3, s);
+    count_launch(3);
+    VIE_CHECK_LAUNCH();
+    if (!gexec) {
+      // one Arnoldi step as a graph: its kernels read j and the stop flag
+      // from device memory, so the same graph serves every step
+      // capture on a private stream (the plan stream may be the legacy
+      // default stream, which cannot be captured); the graph is launched on
+      // the plan stream
+      cudaGraph_t graph;
+      VIE_CUDA(cudaStreamSynchronize(st));
+      P->st = K.cap;
+      cudaError_t cb = cudaStreamBeginCapture(K.cap, cudaStreamCaptureModeRelaxed);
+      if (cb != cudaSuccess) { P->st = st; set_error("graph capture: %s", cudaGetErrorString(cb)); return VIE_ECUDA; }
+      const long long before = launches_total();
+      vie_status es = enqueue_step<C>(P);
+      K.step_launches = (int)(launches_total() - before);
+      count_launch(-K.step_launches);
+      cudaError_t ce = cudaStreamEndCapture(K.cap, &graph);
+      P->st = st;
+      if (es < 0) return es;
+      if (ce != cudaSuccess) { set_error("graph capture: %s", cudaGetErrorString(ce)); return VIE_ECUDA; }
+      VIE_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+      cudaGraphDestroy(graph);
+    }
+    // run steps in chunks, polling the stop flag
+    int done = 0, steps_cycle = 0;
+    const int cyc = std::min(K.restart, max_iter - total);
+    while (!done && steps_cycle < cyc) {
+      const int chunk = std::min(4, cyc - steps_cycle);
+      for (int c = 0; c < chunk; ++c) VIE_CUDA(cudaGraphLaunch(gexec, st));
+      count_launch(chunk * step_kernels(P));
+      steps_cycle += chunk;
+      VIE_CUDA(cudaMemcpyAsync(K.hflag, &s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      VIE_CUDA(cudaMemcpyAsync(K.hflag + 1, &s->iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+      VIE_CUDA(cudaStreamSynchronize(st));
+      done = K.hflag[0];
+    }
+    int hk = 0;
+    VIE_CUDA(cudaMemcpyAsync(&hk, &s->k, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // x += P^-1 (V y)
+    k_solve_y<<<1, 32, 0, st>>>(s);
+    k_combine<C><<<grid_for(n3), 256, 0, st>>>(V, u, n3, s);
+    count_launch(2);
+    VIE_TRY(op_Pinv<C>(P, u, z));
+    VIE_TRY(axpy_same<C>(x, z, n3, st));
+    // true residual rwork = rhs - A x
+    VIE_TRY(op_A<C>(P, x, w));
+    VIE_TRY(sub_same<C>(rhs, w, rwork, n3, st));
+    k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rwork, n3, part);
+    k_norm_final<<<1, 32, 0, st>>>(part, NPART, scal, 1);
+    count_launch(2);
+    VIE_CUDA(cudaMemcpyAsync(hsc + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    VIE_CHECK_LAUNCH();
+    total += hk;
+    rr = hsc[1] / bnorm;
+    if (rr <= tol || hk == 0) break;
+  }
+  *iters = total;
+  *relres = rr;
+  return VIE_OK;
+}
+
+
+void reset_graphs(vie_plan_s* P) {
+  if (!P->kry) return;
+  if (P->kry->g64) { cudaGraphExecDestroy(P->kry->g64); P->kry->g64 = nullptr; }
+  if (P->kry->g128) { cudaGraphExecDestroy(P->kry->g128); P->kry->g128 = nullptr; }
+}
+
+static vie_status norm128(vie_plan_s* P, const double2* v, int idx, double* out) {
+  Krylov& K = *P->kry;
+  double2* part = K.partial.as<double2>();
+  k_norm_partial<double2><<<NPART, RED_THREADS, 0, P->st>>>(v, K.n3, part);
+  k_norm_final<<<1, 32, 0, P->st>>>(part, NPART, K.scal.as<double>(), idx);
+  count_launch(2);
+  VIE_CHECK_LAUNCH();
+  VIE_CUDA(cudaMemcpyAsync(out, K.scal.as<double>() + idx, sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  VIE_CUDA(cudaStreamSynchronize(P->st));
+  return VIE_OK;
+}
+
+// (I - M N) w = M e_inc
+vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!P->has_eps) { set_error("vie_solve: permittivity not set"); return VIE_ESTATE; }
+  if (!P->prec_built) VIE_TRY(precond_build(P));
+  const bool mixed = P->opts.precision == VIE_MIXED;
+  VIE_TRY(krylov_alloc(P, mixed, !mixed));
+  Krylov& K = *P->kry;
+  cudaStream_t st = P->st;
+  const long long n3 = K.n3;
+  const long long N = n3 / 3;
+  double2* b = K.b128.as<double2>();
+  double2* x = K.x128.as<double2>();
+  double2* r = K.r128.as<double2>();
+  double2* t = K.t128.as<double2>();
+  k_rhs<<<grid_for(n3), 256, 0, st>>>(P->M128.as<double2>(), e_inc, b, N);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  double bnorm = 0;
+  VIE_TRY(norm128(P, b, 2, &bnorm));
+  int inner = 0, outer = 0;
+  double relres = 0;
+  const double tol = P->opts.tol;
+  if (bnorm == 0.0) {
+    VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n3, st));
+  } else if (!mixed) {
+    int it = 0;
+    double rr = 0;
+    VIE_TRY(gmres<double2>(P, b, x, r, tol, P->opts.max_iter, &it, &rr));
+    inner = it;
+    outer = 1;
+  } else {
+    VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n3, st));
+    VIE_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, st));
+    double rn = bnorm;
+    while (outer < P->opts.max_refine && inner < P->opts.max_iter) {
+      if (rn <= tol * bnorm) break;
+      // rhs64 = r / ||r||  (scal[3] holds ||r||)
+      VIE_TRY(norm128(P, r, 3, &rn));
+      if (rn <= tol * bnorm) break;
+      k_narrow_scaled<<<grid_for(n3), 256, 0, st>>>(r, K.rhs64.as<float2>(), n3, K.scal.as<double>(), 3);
+      count_launch();
+      int it = 0;
+      double rr = 0;
+      VIE_TRY(gmres<float2>(P, K.rhs64.as<float2>(), K.d64.as<float2>(), K.r64.as<float2>(), P->opts.inner_tol,
+                            P->opts.max_iter - inner, &it, &rr));
+      inner += it;
+      // x += ||r|| d ; r = b - A x (FP64)
+      k_axpy_to64<float2><<<grid_for(n3), 256, 0, st>>>(x, K.d64.as<float2>(), n3, K.scal.as<double>(), 3);
+      count_launch();
+      VIE_TRY(op_A<double2>(P, x, t));
+      k_sub<<<grid_for(n3), 256, 0, st>>>(b, t, r, n3);
+      count_launch();
+      VIE_CHECK_LAUNCH();
+      ++outer;
+      VIE_TRY(norm128(P, r, 3, &rn));
+      if (it == 0) break;
+    }
+  }
+  // final FP64 residual
+  VIE_TRY(op_A<double2>(P, x, t));
+  k_sub<<<grid_for(n3), 256, 0, st>>>(b, t, r, n3);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  double rn = 0;
+  VIE_TRY(norm128(P, r, 4, &rn));
+  relres = bnorm > 0 ? rn / bnorm : 0.0;
+  VIE_CUDA(cudaMemcpyAsync(w_out, x, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    info->iters_inner = inner;
+    info->iters_outer = outer;
+    info->relres = relres;
+    info->precond_bytes = P->precond_bytes;
+    info->kept_fraction = P->kept_fraction;
+    info->t_setup_ms = P->t_setup_ms;
+    info->t_solve_ms = ms;
+  }
+  return relres <= tol ? VIE_OK : VIE_ENOCONV;
+}
+
+}  // namespace vie

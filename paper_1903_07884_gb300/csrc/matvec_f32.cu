@@ -1,0 +1,7 @@
+// complex-FP32 instantiation of the FFT matvec (see matvec_impl.cuh)
+#include "matvec_impl.cuh"
+
+namespace vie {
+template vie_status matvec<float2>(vie_plan_s*, const float2*, float2*, const float2*, const float2*, float2*,
+                                   float2*, cudaStream_t);
+}  // namespace vie

@@ -1,0 +1,314 @@
+// y = A x = x - M (x + G x) through the circulant embedding of the 3-level
+// Toeplitz blocks of G (Sec. 1: O(n log n) FFT product; Sec. 2 Eq. sys_mat).
+//
+// Three passes per matvec, every transform in shared memory:
+//   A  (yz forward)  per component b and group of XG consecutive x: zero-pad
+//      the ny x nz slabs to Py x Pz, 2-D FFT, write T[b][kz][ky][x].
+//   B  (x pass)      per (ky, kz): the three x-lines of length nx, zero-padded
+//      to L, forward FFT, 3x3 symmetric tensor product with the generator
+//      spectra, inverse FFT, keep x < nx, write back to T.
+//   C  (yz inverse)  per component a and x group: inverse 2-D FFT, crop to
+//      ny x nz, epilogue y = x - M (x + Gx).
+// The generator spectra hold only the non-negative octant; the other octants
+// follow from the parity of each component (sign flips).  The inverse
+// normalisation 1/(L Py Pz) is folded into the stored spectra.
+#pragma once
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace vie {
+
+// parity sign of pair c under reversal of axis (0 x, 1 y, 2 z)
+__device__ __forceinline__ float pair_parity(int c, int axis) {
+  const int A[6] = {0, 0, 0, 1, 1, 2};
+  const int B[6] = {0, 1, 2, 1, 2, 2};
+  return ((A[c] == axis) != (B[c] == axis)) ? -1.f : 1.f;
+}
+
+template <class C, int MAXE>
+__global__ void __launch_bounds__(1024) k_mv_yz_fwd(const C* __restrict__ x, C* __restrict__ T, MvDims d,
+                                                    FftPlanDev py, FftPlanDev pz, int XG) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int b = blockIdx.y;
+  const int x0 = blockIdx.x * XG;
+  const int xg = min(XG, d.nx - x0);
+  const int SP = d.Py * d.Pz + 1;
+  const int total = xg * SP;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) s[e] = czero<C>();
+  __syncthreads();
+  const long long plane = (long long)d.ny * d.nx;
+  const C* xb = x + (long long)b * d.nz * plane;
+  const int nin = xg * d.ny * d.nz;
+  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
+    const int xl = e % xg;
+    const int r = e / xg;
+    const int y = r % d.ny, z = r / d.ny;
+    s[xl * SP + z * d.Py + y] = xb[(long long)z * plane + (long long)y * d.nx + x0 + xl];
+  }
+  __syncthreads();
+  {  // y lines (only the nz non-zero rows)
+    SmemLines L{xg * d.nz, d.nz, d.Py, SP, 1, 0};
+    fft_smem<MAXE>(s, py, L, -1);
+  }
+  {  // z lines (all Py columns)
+    SmemLines L{xg * d.Py, d.Py, 1, SP, d.Py, 1};
+    fft_smem<MAXE>(s, pz, L, -1);
+  }
+  const int nout = xg * d.Py * d.Pz;
+  C* Tb = T + (long long)b * d.Pz * d.Py * d.nx;
+  for (int e = threadIdx.x; e < nout; e += blockDim.x) {
+    const int xl = e % xg;
+    const int r = e / xg;
+    const int ky = r % d.Py, kz = r / d.Py;
+    Tb[((long long)kz * d.Py + ky) * d.nx + x0 + xl] = s[xl * SP + kz * d.Py + ky];
+  }
+}
+
+// fetch G^{c}(kx, ky, kz) from the stored octant
+template <class C>
+__device__ __forceinline__ C spec_at(const C* __restrict__ spec, int c, int kx, int kyo, int kzo, float syz_c,
+                                     const MvDims& d, long long Q) {
+  const bool fx = kx > d.L / 2;
+  const int kxo = fx ? d.L - kx : kx;
+  C v = spec[(long long)c * Q + ((long long)kzo * d.Pyh + kyo) * d.Lh + kxo];
+  float sg = syz_c;
+  if (fx) sg *= pair_parity(c, 0);
+  if (sg < 0) { v.x = -v.x; v.y = -v.y; }
+  return v;
+}
+
+template <class C>
+__device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, int kz, const C* __restrict__ spec,
+                                           const MvDims& d) {
+  const bool fy = ky > d.Py / 2, fz = kz > d.Pz / 2;
+  const int kyo = fy ? d.Py - ky : ky;
+  const int kzo = fz ? d.Pz - kz : kz;
+  const long long Q = (long long)d.Lh * d.Pyh * d.Pzh;
+  float syz[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float sg = 1.f;
+    if (fy) sg *= pair_parity(c, 1);
+    if (fz) sg *= pair_parity(c, 2);
+    syz[c] = sg;
+  }
+  for (int kx = threadIdx.x; kx < L; kx += blockDim.x) {
+    const C X0 = s0[kx], X1 = s1[kx], X2 = s2[kx];
+    const C gxx = spec_at(spec, 0, kx, kyo, kzo, syz[0], d, Q);
+    const C gxy = spec_at(spec, 1, kx, kyo, kzo, syz[1], d, Q);
+    const C gxz = spec_at(spec, 2, kx, kyo, kzo, syz[2], d, Q);
+    const C gyy = spec_at(spec, 3, kx, kyo, kzo, syz[3], d, Q);
+    const C gyz = spec_at(spec, 4, kx, kyo, kzo, syz[4], d, Q);
+    const C gzz = spec_at(spec, 5, kx, kyo, kzo, syz[5], d, Q);
+    C y0 = cmul(gxx, X0), y1 = cmul(gxy, X0), y2 = cmul(gxz, X0);
+    cfma(y0, gxy, X1); cfma(y1, gyy, X1); cfma(y2, gyz, X1);
+    cfma(y0, gxz, X2); cfma(y1, gyz, X2); cfma(y2, gzz, X2);
+    s0[kx] = y0; s1[kx] = y1; s2[kx] = y2;
+  }
+}
+
+// fused x pass: shared memory holds the three x-lines of one (ky, kz)
+template <class C, int MAXE>
+__global__ void __launch_bounds__(1024) k_mv_x(C* __restrict__ T, const C* __restrict__ spec, MvDims d,
+                                               FftPlanDev pl, int joint) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int kyz = blockIdx.x;
+  const int ky = kyz % d.Py, kz = kyz / d.Py;
+  const int L = d.L;
+  const long long lstride = (long long)d.Pz * d.Py * d.nx;
+  const long long loff = ((long long)kz * d.Py + ky) * d.nx;
+  for (int e = threadIdx.x; e < 3 * L; e += blockDim.x) {
+    const int b = e / L, i = e - b * L;
+    s[e] = i < d.nx ? T[b * lstride + loff + i] : czero<C>();
+  }
+  __syncthreads();
+  if (joint) {
+    SmemLines Ls{3, 3, L, 0, 1, 0};
+    fft_smem<MAXE>(s, pl, Ls, -1);
+  } else {
+    for (int b = 0; b < 3; ++b) {
+      SmemLines Ls{1, 1, 0, 0, 1, 0};
+      fft_smem<MAXE>(s + b * L, pl, Ls, -1);
+    }
+  }
+  tensor_mul(s, s + L, s + 2 * L, L, ky, kz, spec, d);
+  __syncthreads();
+  if (joint) {
+    SmemLines Ls{3, 3, L, 0, 1, 0};
+    fft_smem<MAXE>(s, pl, Ls, +1);
+  } else {
+    for (int b = 0; b < 3; ++b) {
+      SmemLines Ls{1, 1, 0, 0, 1, 0};
+      fft_smem<MAXE>(s + b * L, pl, Ls, +1);
+    }
+  }
+  for (int e = threadIdx.x; e < 3 * d.nx; e += blockDim.x) {
+    const int a = e / d.nx, i = e - a * d.nx;
+    T[a * lstride + loff + i] = s[a * L + i];
+  }
+}
+
+// unfused x pass, step 2: tensor product on the full spectrum S[3][Pz][Py][L]
+template <class C>
+__global__ void k_mv_xmul(C* __restrict__ S, const C* __restrict__ spec, MvDims d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  (void)smem_raw;
+  const int kyz = blockIdx.x;
+  const int ky = kyz % d.Py, kz = kyz / d.Py;
+  const long long lstride = (long long)d.Pz * d.Py * d.L;
+  C* s0 = S + ((long long)kz * d.Py + ky) * d.L;
+  tensor_mul(s0, s0 + lstride, s0 + 2 * lstride, d.L, ky, kz, spec, d);
+}
+
+template <class C, int MAXE>
+__global__ void __launch_bounds__(1024) k_mv_yz_inv(const C* __restrict__ T, const C* __restrict__ x,
+                                                    const C* __restrict__ Mv, C* __restrict__ y, MvDims d,
+                                                    FftPlanDev py, FftPlanDev pz, int XG) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int a = blockIdx.y;
+  const int x0 = blockIdx.x * XG;
+  const int xg = min(XG, d.nx - x0);
+  const int SP = d.Py * d.Pz + 1;
+  const C* Ta = T + (long long)a * d.Pz * d.Py * d.nx;
+  const int nin = xg * d.Py * d.Pz;
+  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
+    const int xl = e % xg;
+    const int r = e / xg;
+    const int ky = r % d.Py, kz = r / d.Py;
+    s[xl * SP + kz * d.Py + ky] = Ta[((long long)kz * d.Py + ky) * d.nx + x0 + xl];
+  }
+  __syncthreads();
+  {  // z lines (all Py columns)
+    SmemLines L{xg * d.Py, d.Py, 1, SP, d.Py, 1};
+    fft_smem<MAXE>(s, pz, L, +1);
+  }
+  {  // y lines (only the nz rows kept)
+    SmemLines L{xg * d.nz, d.nz, d.Py, SP, 1, 0};
+    fft_smem<MAXE>(s, py, L, +1);
+  }
+  const long long plane = (long long)d.ny * d.nx;
+  const long long off_a = (long long)a * d.nz * plane;
+  const int nout = xg * d.ny * d.nz;
+  for (int e = threadIdx.x; e < nout; e += blockDim.x) {
+    const int xl = e % xg;
+    const int r = e / xg;
+    const int yy = r % d.ny, z = r / d.ny;
+    const long long v = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
+    const C xv = x[off_a + v];
+    const C m = Mv[v];
+    const C g = s[xl * SP + z * d.Py + yy];
+    // y = x - M (x + Gx)
+    const C t = cadd(xv, g);
+    y[off_a + v] = csub(xv, cmul(m, t));
+  }
+}
+
+static inline int pick_xg(const MvDims& d, size_t csize) {
+  const size_t slab = (size_t)(d.Py * d.Pz + 1) * csize;
+  int xg = 32;
+  while (xg > 2 && (size_t)xg * slab > 96 * 1024) xg /= 2;
+  if (xg > d.nx) xg = std::max(1, d.nx);
+  return xg;
+}
+
+template <class C> static FftPlanDev planof(const FftLen& f);
+template <> inline FftPlanDev planof<double2>(const FftLen& f) { return f.pn64; }
+template <> inline FftPlanDev planof<float2>(const FftLen& f) { return f.pn32; }
+
+static inline int threads_for(long long E, int& maxe, int cap_per) {
+  int threads = 128;
+  while (threads < 1024 && E > (long long)cap_per * threads) threads *= 2;
+  const long long per = (E + threads - 1) / threads;
+  maxe = per <= 8 ? 8 : per <= 16 ? 16 : 32;
+  return threads;
+}
+
+template <class K>
+static vie_status set_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return VIE_OK;
+}
+
+#define VIE_DISPATCH_MAXE(ME, CALL)                                             \
+  switch (ME) {                                                                 \
+    case 8: CALL(8); break;                                                     \
+    case 16: CALL(16); break;                                                   \
+    default: set_error("matvec: tile too large for one block"); return VIE_EINVAL; \
+  }
+
+template <class C>
+vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C* T, C* S, cudaStream_t st) {
+  const MvDims& d = P->d;
+  const int cap = 16;
+  // pass A
+  const int XG = pick_xg(d, sizeof(C));
+  const size_t smemA = (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
+  int meA;
+  const int thA = threads_for((long long)XG * d.Py * d.Pz, meA, cap);
+  dim3 gA(ceil_div(d.nx, XG), 3);
+  const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
+#define CALL_A(ME)                                                         \
+  {                                                                        \
+    auto k = k_mv_yz_fwd<C, ME>;                                           \
+    VIE_TRY(set_smem(k, smemA));                                           \
+    k<<<gA, thA, smemA, st>>>(x, T, d, py, pz, XG);                        \
+  }
+  VIE_DISPATCH_MAXE(meA, CALL_A)
+#undef CALL_A
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  // pass B
+  const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
+  if (fused) {
+    const size_t smemB = (size_t)3 * d.L * sizeof(C);
+    int meB;
+    int joint = 1;
+    int thB = threads_for(3LL * d.L, meB, cap);
+    if ((long long)meB * thB < 3LL * d.L || meB > cap) {
+      joint = 0;
+      thB = threads_for((long long)d.L, meB, cap);
+    }
+    if ((long long)meB * thB < (joint ? 3LL : 1LL) * d.L) { set_error("matvec: x line too long"); return VIE_EINVAL; }
+#define CALL_B(ME)                                                         \
+  {                                                                        \
+    auto k = k_mv_x<C, ME>;                                                \
+    VIE_TRY(set_smem(k, smemB));                                           \
+    k<<<d.Py * d.Pz, thB, smemB, st>>>(T, spec, d, pl, joint);             \
+  }
+    VIE_DISPATCH_MAXE(meB, CALL_B)
+#undef CALL_B
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  } else {
+    // forward x-FFT of every padded line into S, tensor product, inverse into T
+    const int nl = 3 * d.Py * d.Pz;
+    LineDesc lf = lines_flat(d.nx, d.L, nl, d.nx, 1, d.L, 1);
+    if (!S) { set_error("matvec: missing x-spectrum scratch"); return VIE_EINVAL; }
+    VIE_TRY(fft_lines<C>(T, S, lf, *P->fL, -1, 1.0, nullptr, st));
+    k_mv_xmul<C><<<d.Py * d.Pz, 256, 0, st>>>(S, spec, d);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    LineDesc li = lines_flat(d.L, d.nx, nl, d.L, 1, d.nx, 1);
+    VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, nullptr, st));
+  }
+  // pass C
+#define CALL_C(ME)                                                         \
+  {                                                                        \
+    auto k = k_mv_yz_inv<C, ME>;                                           \
+    VIE_TRY(set_smem(k, smemA));                                           \
+    k<<<gA, thA, smemA, st>>>(T, x, Mv, y, d, py, pz, XG);                 \
+  }
+  VIE_DISPATCH_MAXE(meA, CALL_C)
+#undef CALL_C
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+
+}  // namespace vie

@@ -1,0 +1,788 @@
+// Block-diagonal 1-level circulant preconditioner (Sec. 4, Sec. 5.1.1,
+// Sec. 5.2, Sec. 5.3).
+//
+// Per box (nx_b x ny_b x nz_b voxels, m = 3 ny_b nz_b unknowns per x-slab,
+// rows ordered [alpha][z][y]):
+//  1. homogenise M over the box (Sec. 5.2: mode, x-mean, or real x-mean);
+//  2. for each generator pair and transverse offset, the Chan vector of the
+//     x-Toeplitz line (Eq. Chan) and its DFT lambda_f (C = F^-1 Lambda F);
+//  3. proxy v_f (Eqs. proxy1-proxy2) and the kept set K = {f : v^_f > tau};
+//  4. D_f = I - M~ (I + Lambda_f) (Eq. Di) for the stored frequencies;
+//  5. FP64 LU with partial pivoting of every stored block, then the explicit
+//     inverse (complex FP32 for the mixed path, FP64 for the FP64 path);
+//  6. apply: z = F^-1 P^T diag(D_f^-1) P F r (the C_B^-1 display of Sec. 4).
+// Only f <= n/2 carry blocks: the x-parity of the generators gives
+// D_{n-f} = S D_f S, S = diag(-1 on x-component rows, +1 otherwise), so f and
+// n - f share one block read.  Frequencies outside K use the central block
+// D_{ceil(n/2)} (1-based) through one multi-right-hand-side product.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "greens.cuh"
+#include "internal.h"
+
+namespace vie {
+
+
+__device__ __forceinline__ int pair_code(int a, int b) {
+  if (a > b) { int t = a; a = b; b = t; }
+  // xx0 xy1 xz2 yy3 yz4 zz5
+  return a == 0 ? b : (a == 1 ? 2 + b : 5);
+}
+
+struct BoxDims {
+  int x0, y0, z0, n, ny, nz, m;
+  int gnx, gny, gnz;   // full grid
+};
+
+// ---------------------------------------------------------------------------
+// 1. homogenisation
+// ---------------------------------------------------------------------------
+__global__ void k_hom_mean(const double2* __restrict__ M, double2* __restrict__ Mt, BoxDims b, int real_only) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.ny * b.nz) return;
+  const int yb = t % b.ny, zb = t / b.ny;
+  const double2* row = M + ((long long)(b.z0 + zb) * b.gny + (b.y0 + yb)) * b.gnx + b.x0;
+  double sr = 0, si = 0;
+  for (int x = 0; x < b.n; ++x) { sr += row[x].x; si += row[x].y; }
+  sr /= b.n;
+  si /= b.n;
+  Mt[t] = make_double2(sr, real_only ? 0.0 : si);
+}
+
+// Mode of all box entries: one block keeps a table of distinct values and
+// counts.  Ties go to the smallest |value|, then the smallest (re, im).
+constexpr int MODE_MAXV = 512;
+__global__ void __launch_bounds__(1024) k_hom_mode(const double2* __restrict__ M, double2* __restrict__ Mt, BoxDims b,
+                                                   int* __restrict__ err) {
+  __shared__ double2 vals[MODE_MAXV];
+  __shared__ int counts[MODE_MAXV];
+  __shared__ double2 chunk[1024];
+  __shared__ int found[1024];
+  __shared__ int nv;
+  __shared__ int overflow;
+  if (threadIdx.x == 0) { nv = 0; overflow = 0; }
+  for (int i = threadIdx.x; i < MODE_MAXV; i += blockDim.x) counts[i] = 0;
+  __syncthreads();
+  const long long total = (long long)b.n * b.ny * b.nz;
+  for (long long base = 0; base < total; base += blockDim.x) {
+    const long long e = base + threadIdx.x;
+    const int nloc = (int)min((long long)blockDim.x, total - base);
+    double2 v = make_double2(0, 0);
+    int idx = -1;
+    if (e < total) {
+      const int x = (int)(e % b.n);
+      const long long r = e / b.n;
+      const int yb = (int)(r % b.ny), zb = (int)(r / b.ny);
+      v = M[((long long)(b.z0 + zb) * b.gny + (b.y0 + yb)) * b.gnx + b.x0 + x];
+      const int cur = nv;
+      for (int j = 0; j < cur; ++j)
+        if (vals[j].x == v.x && vals[j].y == v.y) { idx = j; break; }
+      if (idx >= 0) atomicAdd(&counts[idx], 1);
+      chunk[threadIdx.x] = v;
+      found[threadIdx.x] = idx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < nloc; ++t) {
+        if (found[t] >= 0) continue;
+        const double2 w = chunk[t];
+        int j = 0;
+        for (; j < nv; ++j)
+          if (vals[j].x == w.x && vals[j].y == w.y) break;
+        if (j == nv) {
+          if (nv >= MODE_MAXV) { overflow = 1; continue; }
+          vals[nv] = w;
+          counts[nv] = 0;
+          ++nv;
+        }
+        counts[j] += 1;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int j = 1; j < nv; ++j) {
+      const double aj = vals[j].x * vals[j].x + vals[j].y * vals[j].y;
+      const double ab = vals[best].x * vals[best].x + vals[best].y * vals[best].y;
+      bool better = counts[j] > counts[best];
+      if (counts[j] == counts[best]) {
+        if (aj < ab) better = true;
+        else if (aj == ab && (vals[j].x < vals[best].x || (vals[j].x == vals[best].x && vals[j].y < vals[best].y)))
+          better = true;
+      }
+      if (better) best = j;
+    }
+    const double2 mv = nv ? vals[best] : make_double2(0, 0);
+    for (int t = 0; t < b.ny * b.nz; ++t) Mt[t] = mv;
+    if (overflow) *err = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Chan coefficients of every x-Toeplitz line (Eq. Chan):
+//    c_k = ((n - k) t_k + k t_{k-n}) / n,  t_i = G^c(i, dy, dz)
+// lines ordered (c, dz + nz - 1, dy + ny - 1); output [line][k]
+// ---------------------------------------------------------------------------
+__global__ void k_chan_coeffs(double2* __restrict__ out, BoxDims b, double h, double kb, double2 self) {
+  const int ndy = 2 * b.ny - 1, ndz = 2 * b.nz - 1;
+  const long long nl = 6LL * ndz * ndy;
+  const long long total = nl * b.n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % b.n);
+    const long long line = idx / b.n;
+    const int dyi = (int)(line % ndy);
+    const long long r = line / ndy;
+    const int dzi = (int)(r % ndz);
+    const int c = (int)(r / ndz);
+    const int dy = dyi - (b.ny - 1), dz = dzi - (b.nz - 1);
+    const double2 tk = gen_entry(c, k, dy, dz, h, kb, self);
+    double2 v;
+    if (k == 0) {
+      v = tk;
+    } else {
+      const double2 tm = gen_entry(c, k - b.n, dy, dz, h, kb, self);
+      const double wn = (double)(b.n - k) / b.n, wk = (double)k / b.n;
+      v = make_double2(wn * tk.x + wk * tm.x, wn * tk.y + wk * tm.y);
+    }
+    out[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. proxy and selection (one block).  lam is frequency-major [f][line].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_select(const double2* __restrict__ lam, const double2* __restrict__ Mt,
+                                                 BoxDims b, double tau, double* __restrict__ vhat,
+                                                 int* __restrict__ fmap, int* __restrict__ fsgn,
+                                                 int* __restrict__ disc, int* __restrict__ blkf,
+                                                 int* __restrict__ counts) {
+  const int n = b.n;
+  const int ndy = 2 * b.ny - 1, ndz = 2 * b.nz - 1;
+  const int nl = 6 * ndz * ndy;
+  const int cstar = ((b.ny + 1) / 2) * ((b.nz + 1) / 2) - 1;
+  int line;
+  bool diag = false;
+  if (cstar == 0) {
+    line = (0 * ndz + (b.nz - 1)) * ndy + (b.ny - 1);
+    diag = true;
+  } else {
+    const int zq = (cstar % (b.ny * b.nz)) / b.ny, yq = cstar % b.ny;
+    line = (0 * ndz + (-zq + b.nz - 1)) * ndy + (-yq + b.ny - 1);
+  }
+  __shared__ double red[1024];
+  double mx = 0.0;
+  for (int f = threadIdx.x; f < n; f += blockDim.x) {
+    double2 v = lam[(long long)f * nl + line];
+    if (diag) {
+      const double2 m0 = Mt[0];
+      // 1 - M0 (1 + lambda)
+      const double ar = 1.0 + v.x, ai = v.y;
+      v = make_double2(1.0 - (m0.x * ar - m0.y * ai), -(m0.x * ai + m0.y * ar));
+    }
+    const double a = sqrt(v.x * v.x + v.y * v.y);
+    vhat[f] = a;
+    mx = fmax(mx, a);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double vmax = red[0];
+  __syncthreads();
+  for (int f = threadIdx.x; f < n; f += blockDim.x) vhat[f] = vmax > 0 ? vhat[f] / vmax : 1.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int half = n / 2;
+    const int rep = (n + 1) / 2 - 1;
+    int nb = 0;
+    // slots for kept f <= n/2 (kept decided at the folded frequency)
+    for (int f = 0; f <= half; ++f) {
+      const bool keep = tau <= 0.0 || vhat[f] > tau;
+      if (keep) { blkf[nb] = f; fmap[f] = nb; ++nb; } else fmap[f] = -1;
+    }
+    const int nks = nb;
+    int rep_slot = fmap[rep];
+    if (rep_slot < 0) { blkf[nb] = rep; rep_slot = nb; ++nb; }
+    int nd = 0, nk = 0;
+    for (int f = 0; f < n; ++f) {
+      const int fo = f <= half ? f : n - f;
+      const int s = fmap[fo];
+      if (f > half) fmap[f] = s;
+      fsgn[f] = (f > half) ? 1 : 0;
+      if (s < 0) disc[nd++] = f; else ++nk;
+    }
+    counts[0] = nb;
+    counts[1] = nk;
+    counts[2] = nd;
+    counts[3] = rep_slot;
+    counts[4] = nks;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. block assembly D_f[p][q] = delta - M~_p (delta + lambda_f^{pq}), column-major
+// ---------------------------------------------------------------------------
+__global__ void k_block_assemble(double2* __restrict__ D, const double2* __restrict__ lam,
+                                 const double2* __restrict__ Mt, const int* __restrict__ blkf, BoxDims b, int nblk) {
+  const int m = b.m;
+  const int ndy = 2 * b.ny - 1, ndz = 2 * b.nz - 1;
+  const int nl = 6 * ndz * ndy;
+  const int yz = b.ny * b.nz;
+  const long long total = (long long)nblk * m * m;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(idx % m);
+    const long long r = idx / m;
+    const int q = (int)(r % m);
+    const int s = (int)(r / m);
+    const int f = blkf[s];
+    const int ap = p / yz, zp = (p % yz) / b.ny, yp = p % b.ny;
+    const int aq = q / yz, zq = (q % yz) / b.ny, yq = q % b.ny;
+    const int c = pair_code(ap, aq);
+    const int line = (c * ndz + (zp - zq + b.nz - 1)) * ndy + (yp - yq + b.ny - 1);
+    const double2 l = lam[(long long)f * nl + line];
+    const double2 mp = Mt[zp * b.ny + yp];
+    const double dl = (p == q) ? 1.0 : 0.0;
+    const double ar = dl + l.x, ai = l.y;
+    D[idx] = make_double2(dl - (mp.x * ar - mp.y * ai), -(mp.x * ai + mp.y * ar));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5a. batched FP64 LU with partial pivoting (column-major, one block per
+//     matrix, right-looking with panels of NB columns).
+// ---------------------------------------------------------------------------
+constexpr int LU_NB = 16;
+
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+
+__global__ void __launch_bounds__(512) k_block_lu(double2* __restrict__ Aall, int* __restrict__ pivall, int m,
+                                                  int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* P = reinterpret_cast<double2*>(smem_raw);     // panel: NB columns x (m - k0) rows
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int piv_s;
+  double2* A = Aall + (long long)blockIdx.x * m * m;
+  int* piv = pivall + (long long)blockIdx.x * m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int k0 = 0; k0 < m; k0 += LU_NB) {
+    const int nb = min(LU_NB, m - k0);
+    const int rows = m - k0;
+    // load panel
+    for (int e = tid; e < nb * rows; e += nt) {
+      const int j = e / rows, i = e - j * rows;
+      P[j * rows + i] = A[(long long)(k0 + j) * m + k0 + i];
+    }
+    __syncthreads();
+    for (int kk = 0; kk < nb; ++kk) {
+      const int k = k0 + kk;
+      double2* col = P + kk * rows;
+      // pivot search over rows k..m-1 (first maximum of |re| + |im|)
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = kk + tid; i < rows; i += nt) {
+        const double v = cabs1(col[i]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double b0 = rv[0];
+        int i0 = ri[0];
+        for (int w = 1; w < nw; ++w)
+          if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+        piv_s = i0;
+        piv[k] = k0 + i0;
+        if (b0 == 0.0) atomicExch(info, 1);
+      }
+      __syncthreads();
+      const int pi = piv_s;
+      // swap rows kk and pi inside the panel
+      if (pi != kk) {
+        for (int j = tid; j < nb; j += nt) {
+          const double2 t = P[j * rows + kk];
+          P[j * rows + kk] = P[j * rows + pi];
+          P[j * rows + pi] = t;
+        }
+      }
+      __syncthreads();
+      const double2 pv = col[kk];
+      const double2 ipv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0, 0) : cinv(pv);
+      for (int i = kk + 1 + tid; i < rows; i += nt) col[i] = cmul(col[i], ipv);
+      __syncthreads();
+      // rank-1 update of the remaining panel columns
+      const int rem = nb - kk - 1;
+      for (int e = tid; e < rem * (rows - kk - 1); e += nt) {
+        const int jj = kk + 1 + e / (rows - kk - 1);
+        const int i = kk + 1 + e % (rows - kk - 1);
+        double2 a = P[jj * rows + i];
+        const double2 l = col[i], u = P[jj * rows + kk];
+        a.x -= l.x * u.x - l.y * u.y;
+        a.y -= l.x * u.y + l.y * u.x;
+        P[jj * rows + i] = a;
+      }
+      __syncthreads();
+    }
+    // store panel
+    for (int e = tid; e < nb * rows; e += nt) {
+      const int j = e / rows, i = e - j * rows;
+      A[(long long)(k0 + j) * m + k0 + i] = P[j * rows + i];
+    }
+    // apply the panel's row swaps to the other columns
+    for (int j = tid; j < m; j += nt) {
+      if (j >= k0 && j < k0 + nb) continue;
+      double2* cj = A + (long long)j * m;
+      for (int kk = 0; kk < nb; ++kk) {
+        const int k = k0 + kk, p = piv[k];
+        if (p != k) { const double2 t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
+      }
+    }
+    __syncthreads();
+    const int right = m - k0 - nb;
+    if (right > 0) {
+      // U12 = L11^{-1} A12 (unit lower triangular), one column per thread
+      for (int j = k0 + nb + tid; j < m; j += nt) {
+        double2* cj = A + (long long)j * m + k0;
+        double2 u[LU_NB];
+#pragma unroll
+        for (int t = 0; t < LU_NB; ++t) u[t] = t < nb ? cj[t] : make_double2(0, 0);
+#pragma unroll
+        for (int t = 0; t < LU_NB; ++t) {
+          if (t >= nb) break;
+#pragma unroll
+          for (int i = t + 1; i < LU_NB; ++i) {
+            if (i >= nb) break;
+            const double2 l = P[t * rows + i];
+            u[i].x -= l.x * u[t].x - l.y * u[t].y;
+            u[i].y -= l.x * u[t].y + l.y * u[t].x;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < LU_NB; ++t) if (t < nb) cj[t] = u[t];
+      }
+      __syncthreads();
+      // A22 -= L21 U12: thread per element, i fastest (coalesced columns)
+      const int r22 = m - k0 - nb;
+      for (long long e = tid; e < (long long)r22 * right; e += nt) {
+        const int jj = (int)(e / r22), ii = (int)(e - (long long)jj * r22);
+        const int j = k0 + nb + jj, i = k0 + nb + ii;
+        double2* cj = A + (long long)j * m;
+        double2 a = cj[i];
+#pragma unroll 4
+        for (int t = 0; t < nb; ++t) {
+          const double2 l = P[t * rows + nb + ii];
+          const double2 u = cj[k0 + t];
+          a.x -= l.x * u.x - l.y * u.y;
+          a.y -= l.x * u.y + l.y * u.x;
+        }
+        cj[i] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5b. explicit inverse from the LU factors: solve L U X = P I for a chunk of
+//     CB columns; X written row-major in precision C.
+// ---------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ LUall, const int* __restrict__ pivall,
+                                                   C* __restrict__ invall, int m, int CB) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Y = reinterpret_cast<C*>(smem_raw);   // [m][CB]
+  using T = typename real_of<C>::type;
+  const double2* LU = LUall + (long long)blockIdx.x * m * m;
+  const int* piv = pivall + (long long)blockIdx.x * m;
+  C* inv = invall + (long long)blockIdx.x * m * m;
+  const int j0 = blockIdx.y * CB;
+  const int cb = min(CB, m - j0);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * CB; e += nt) {
+    const int i = e / CB, c = e - i * CB;
+    Y[e] = (c < cb && i == j0 + c) ? cmake<C>(1, 0) : czero<C>();
+  }
+  __syncthreads();
+  // P applied to the identity columns: the row swaps in order
+  if (tid < cb) {
+    for (int k = 0; k < m; ++k) {
+      const int p = piv[k];
+      if (p != k) { const C t = Y[k * CB + tid]; Y[k * CB + tid] = Y[p * CB + tid]; Y[p * CB + tid] = t; }
+    }
+  }
+  __syncthreads();
+  // forward substitution with unit lower L
+  for (int k = 0; k < m - 1; ++k) {
+    const int cnt = (m - k - 1) * cb;
+    for (int e = tid; e < cnt; e += nt) {
+      const int i = k + 1 + e / cb, c = e % cb;
+      const double2 l = LU[(long long)k * m + i];
+      const C lc = cmake<C>((T)l.x, (T)l.y);
+      C y = Y[i * CB + c];
+      const C yk = Y[k * CB + c];
+      y.x -= lc.x * yk.x - lc.y * yk.y;
+      y.y -= lc.x * yk.y + lc.y * yk.x;
+      Y[i * CB + c] = y;
+    }
+    __syncthreads();
+  }
+  // back substitution with U
+  for (int k = m - 1; k >= 0; --k) {
+    if (tid < cb) {
+      const double2 u = LU[(long long)k * m + k];
+      const double2 iu = cinv(u);
+      const C ic = cmake<C>((T)iu.x, (T)iu.y);
+      Y[k * CB + tid] = cmul(Y[k * CB + tid], ic);
+    }
+    __syncthreads();
+    const int cnt = k * cb;
+    for (int e = tid; e < cnt; e += nt) {
+      const int i = e / cb, c = e % cb;
+      const double2 u = LU[(long long)k * m + i];
+      const C uc = cmake<C>((T)u.x, (T)u.y);
+      C y = Y[i * CB + c];
+      const C yk = Y[k * CB + c];
+      y.x -= uc.x * yk.x - uc.y * yk.y;
+      y.y -= uc.x * yk.y + uc.y * yk.x;
+      Y[i * CB + c] = y;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * cb; e += nt) {
+    const int i = e / cb, c = e - i * cb;
+    inv[(long long)i * m + j0 + c] = Y[i * CB + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 6. apply kernels
+// ---------------------------------------------------------------------------
+// Kept blocks: warp per row, the block's rows shared by f and n - f.
+template <class C>
+__global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, const int* __restrict__ blkf,
+                                                    const C* __restrict__ R, C* __restrict__ Z, int m, int n,
+                                                    int ny_nz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* r = reinterpret_cast<C*>(smem_raw);   // [2][m]
+  const int s = blockIdx.x;
+  const int f = blkf[s];
+  const int f2 = (n - f) % n;
+  const bool pair = (f2 != f);
+  const C* D = inv + (long long)s * m * m;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    r[j] = R[(long long)f * m + j];
+    if (pair) {
+      C v = R[(long long)f2 * m + j];
+      if (j < ny_nz) { v.x = -v.x; v.y = -v.y; }
+      r[m + j] = v;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    const C* row = D + (long long)i * m;
+    C a1 = czero<C>(), a2 = czero<C>();
+    for (int j = lane; j < m; j += 32) {
+      const C d = row[j];
+      cfma(a1, d, r[j]);
+      if (pair) cfma(a2, d, r[m + j]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
+      a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
+      a2.x += __shfl_xor_sync(0xffffffffu, a2.x, o);
+      a2.y += __shfl_xor_sync(0xffffffffu, a2.y, o);
+    }
+    if (lane == 0) {
+      Z[(long long)f * m + i] = a1;
+      if (pair) {
+        if (i < ny_nz) { a2.x = -a2.x; a2.y = -a2.y; }
+        Z[(long long)f2 * m + i] = a2;
+      }
+    }
+  }
+}
+
+// Discarded frequencies: Z[f] = D_rep^{-1} R[f] for a tile of FT frequencies.
+template <class C, int FT>
+__global__ void __launch_bounds__(256) k_rep_gemm(const C* __restrict__ Drep, const int* __restrict__ disc, int ndisc,
+                                                  const C* __restrict__ R, C* __restrict__ Z, int m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* r = reinterpret_cast<C*>(smem_raw);   // [FT][m]
+  const int t0 = blockIdx.x * FT;
+  const int nt = min(FT, ndisc - t0);
+  for (int e = threadIdx.x; e < FT * m; e += blockDim.x) {
+    const int t = e / m, j = e - t * m;
+    r[e] = t < nt ? R[(long long)disc[t0 + t] * m + j] : czero<C>();
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    const C* row = Drep + (long long)i * m;
+    C acc[FT];
+#pragma unroll
+    for (int t = 0; t < FT; ++t) acc[t] = czero<C>();
+    for (int j = lane; j < m; j += 32) {
+      const C d = row[j];
+#pragma unroll
+      for (int t = 0; t < FT; ++t) cfma(acc[t], d, r[t * m + j]);
+    }
+#pragma unroll
+    for (int t = 0; t < FT; ++t) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
+        acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
+      }
+    }
+    if (lane < nt) {
+      C v = acc[0];
+#pragma unroll
+      for (int t = 1; t < FT; ++t) if (t == lane) v = acc[t];
+      Z[(long long)disc[t0 + lane] * m + i] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static BoxDims dims_of(const vie_plan_s* P, const vie_box& b) {
+  BoxDims d;
+  d.x0 = b.x0; d.y0 = b.y0; d.z0 = b.z0; d.n = b.nx; d.ny = b.ny; d.nz = b.nz;
+  d.m = 3 * b.ny * b.nz;
+  d.gnx = P->nx; d.gny = P->ny; d.gnz = P->nz;
+  return d;
+}
+
+void precond_free(vie_plan_s* P) {
+  P->bp.clear();
+  P->prec_built = false;
+  P->precond_bytes = 0;
+}
+
+static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128) {
+  const BoxDims bd = dims_of(P, B.b);
+  cudaStream_t st = P->st;
+  const int n = bd.n, m = bd.m;
+  B.n = n; B.m = m;
+  B.rep = (n + 1) / 2 - 1;
+  VIE_TRY(fft_get(n, &B.fx));
+  // 1. homogenise
+  VIE_TRY(B.Mt.alloc(sizeof(double2) * bd.ny * bd.nz));
+  DevBuf err;
+  VIE_TRY(err.alloc(sizeof(int) * 8));
+  VIE_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int) * 8, st));
+  if (P->opts.homog == VIE_HOM_MODE) {
+    k_hom_mode<<<1, 1024, 0, st>>>(P->M128.as<double2>(), B.Mt.as<double2>(), bd, err.as<int>());
+  } else {
+    const int t = bd.ny * bd.nz;
+    k_hom_mean<<<ceil_div(t, 128), 128, 0, st>>>(P->M128.as<double2>(), B.Mt.as<double2>(), bd,
+                                                 P->opts.homog == VIE_HOM_REALMEAN ? 1 : 0);
+  }
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  // 2. Chan coefficients and eigenvalues (frequency-major)
+  const int ndy = 2 * bd.ny - 1, ndz = 2 * bd.nz - 1;
+  const int nl = 6 * ndz * ndy;
+  DevBuf coef;
+  VIE_TRY(coef.alloc(sizeof(double2) * (size_t)nl * n));
+  VIE_TRY(B.lam.alloc(sizeof(double2) * (size_t)nl * n));
+  const double2 self = self_term_value(P->h, P->kb);
+  {
+    const long long total = (long long)nl * n;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    k_chan_coeffs<<<grid, 256, 0, st>>>(coef.as<double2>(), bd, P->h, P->kb, self);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  }
+  {
+    DevBuf tmp;
+    if (B.fx->bluestein) VIE_TRY(tmp.alloc(sizeof(double2) * (size_t)nl * B.fx->M));
+    LineDesc ld = lines_flat(n, n, nl, n, 1, 1, nl);   // out: [f][line]
+    VIE_TRY(fft_lines<double2>(coef.as<double2>(), B.lam.as<double2>(), ld, *B.fx, -1, 1.0, tmp.as<double2>(), st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+  }
+  coef.release();
+  // 3. proxy and selection
+  VIE_TRY(B.vhat.alloc(sizeof(double) * n));
+  VIE_TRY(B.fmap.alloc(sizeof(int) * n));
+  VIE_TRY(B.fsgn.alloc(sizeof(int) * n));
+  VIE_TRY(B.disc.alloc(sizeof(int) * n));
+  VIE_TRY(B.blkf.alloc(sizeof(int) * (n / 2 + 2)));
+  DevBuf cnt;
+  VIE_TRY(cnt.alloc(sizeof(int) * 8));
+  k_select<<<1, 1024, 0, st>>>(B.lam.as<double2>(), B.Mt.as<double2>(), bd, P->opts.reduce_tol, B.vhat.as<double>(),
+                               B.fmap.as<int>(), B.fsgn.as<int>(), B.disc.as<int>(), B.blkf.as<int>(), cnt.as<int>());
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  int hc[8] = {0}, herr[8] = {0};
+  VIE_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (herr[0]) { set_error("mode homogenisation: more than %d distinct values in a box", MODE_MAXV); return VIE_EINVAL; }
+  B.nblk = hc[0];
+  B.nkept = hc[1];
+  B.ndisc = hc[2];
+  B.rep = hc[3];     // now the representative's slot
+  B.nhalf = hc[4];   // number of kept slots (they come first)
+  // 4. assemble the stored blocks (FP64, column-major)
+  DevBuf LU, piv, info;
+  const size_t mm = (size_t)m * m;
+  VIE_TRY(LU.alloc(sizeof(double2) * mm * B.nblk));
+  VIE_TRY(piv.alloc(sizeof(int) * (size_t)m * B.nblk));
+  VIE_TRY(info.alloc(sizeof(int)));
+  VIE_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
+  {
+    const long long total = (long long)mm * B.nblk;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+    k_block_assemble<<<grid, 256, 0, st>>>(LU.as<double2>(), B.lam.as<double2>(), B.Mt.as<double2>(),
+                                           B.blkf.as<int>(), bd, B.nblk);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  }
+  // 5. FP64 LU, then the inverse(s)
+  {
+    const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
+    VIE_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_lu<<<B.nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, info.as<int>());
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  }
+  const int CB = 32;
+  dim3 gi(B.nblk, ceil_div(m, CB));
+  if (want64) {
+    VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
+    const size_t smem = sizeof(float2) * (size_t)m * CB;
+    VIE_CUDA(cudaFuncSetAttribute(k_block_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
+    VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
+    if (B.fx->bluestein) VIE_TRY(B.tmp64.alloc(sizeof(float2) * (size_t)m * B.fx->M));
+  }
+  if (want128) {
+    VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
+    const size_t smem = sizeof(double2) * (size_t)m * CB;
+    VIE_CUDA(cudaFuncSetAttribute(k_block_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    VIE_TRY(B.rhat128.alloc(sizeof(double2) * (size_t)n * m));
+    VIE_TRY(B.zhat128.alloc(sizeof(double2) * (size_t)n * m));
+    if (B.fx->bluestein) VIE_TRY(B.tmp128.alloc(sizeof(double2) * (size_t)m * B.fx->M));
+  }
+  int hinfo = 0;
+  VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (hinfo) { set_error("preconditioner: singular block D_f"); return VIE_EINVAL; }
+  return VIE_OK;
+}
+
+vie_status precond_build(vie_plan_s* P) {
+  precond_free(P);
+  if (P->opts.precond == VIE_PREC_NONE) { P->prec_built = true; P->kept_fraction = 0; return VIE_OK; }
+  const auto t0 = std::chrono::steady_clock::now();
+  const bool want64 = P->opts.precision == VIE_MIXED;
+  const bool want128 = P->opts.precision == VIE_FP64;
+  long long kept = 0, total = 0;
+  size_t bytes = 0;
+  for (const vie_box& b : P->boxes) {
+    std::unique_ptr<BoxPrec> B(new BoxPrec());
+    B->b = b;
+    VIE_TRY(build_box(P, *B, want64, want128));
+    kept += B->nkept;
+    total += B->n;
+    bytes += B->inv64.bytes + B->inv128.bytes;
+    P->bp.push_back(std::move(B));
+  }
+  P->precond_bytes = bytes;
+  P->kept_fraction = total ? (double)kept / total : 0;
+  P->prec_built = true;
+  P->t_setup_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return VIE_OK;
+}
+
+template <class C> struct BoxBufs;
+template <> struct BoxBufs<float2> {
+  static float2* inv(BoxPrec& B) { return B.inv64.as<float2>(); }
+  static float2* rh(BoxPrec& B) { return B.rhat64.as<float2>(); }
+  static float2* zh(BoxPrec& B) { return B.zhat64.as<float2>(); }
+  static float2* tmp(BoxPrec& B) { return B.tmp64.as<float2>(); }
+};
+template <> struct BoxBufs<double2> {
+  static double2* inv(BoxPrec& B) { return B.inv128.as<double2>(); }
+  static double2* rh(BoxPrec& B) { return B.rhat128.as<double2>(); }
+  static double2* zh(BoxPrec& B) { return B.zhat128.as<double2>(); }
+  static double2* tmp(BoxPrec& B) { return B.tmp128.as<double2>(); }
+};
+
+template <class C>
+vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
+  const long long N = (long long)P->nx * P->ny * P->nz;
+  if (!P->prec_built) { set_error("preconditioner not built"); return VIE_ESTATE; }
+  const bool whole = P->bp.size() == 1 && P->boxes[0].nx == P->nx && P->boxes[0].ny == P->ny &&
+                     P->boxes[0].nz == P->nz;
+  if (P->opts.precond == VIE_PREC_NONE || !whole) {
+    VIE_CUDA(cudaMemcpyAsync(z, r, sizeof(C) * 3 * N, cudaMemcpyDeviceToDevice, st));
+    if (P->opts.precond == VIE_PREC_NONE) return VIE_OK;
+  }
+  for (auto& Bp : P->bp) {
+    BoxPrec& B = *Bp;
+    C* inv = BoxBufs<C>::inv(B);
+    if (!inv) { set_error("preconditioner not built for this precision"); return VIE_ESTATE; }
+    const int n = B.n, m = B.m, nyb = B.b.ny, nzb = B.b.nz;
+    C* rh = BoxBufs<C>::rh(B);
+    C* zh = BoxBufs<C>::zh(B);
+    // gather + x-FFT: line p = (alpha, zb, yb) -> R[f][p]
+    LineDesc ld{n, n, m, nyb, nzb,
+                (long long)P->nx, (long long)P->ny * P->nx, N, 1,
+                1, (long long)nyb, (long long)nyb * nzb, (long long)m};
+    const long long base = ((long long)B.b.z0 * P->ny + B.b.y0) * P->nx + B.b.x0;
+    VIE_TRY(fft_lines<C>(r + base, rh, ld, *B.fx, -1, 1.0, BoxBufs<C>::tmp(B), st));
+    // kept blocks (S1 pairs)
+    if (B.nhalf > 0) {
+      const size_t smem = sizeof(C) * 2 * m;
+      k_block_gemv<C><<<B.nhalf, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, n, nyb * nzb);
+      count_launch();
+      VIE_CHECK_LAUNCH();
+    }
+    // discarded frequencies against the representative block
+    if (B.ndisc > 0) {
+      constexpr int FT = 8;
+      const size_t smem = sizeof(C) * FT * m;
+      auto kern = k_rep_gemm<C, FT>;
+      if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<ceil_div(B.ndisc, FT), 256, smem, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m);
+      count_launch();
+      VIE_CHECK_LAUNCH();
+    }
+    // inverse x-FFT + scatter
+    LineDesc lo{n, n, m, nyb, nzb,
+                1, (long long)nyb, (long long)nyb * nzb, (long long)m,
+                (long long)P->nx, (long long)P->ny * P->nx, N, 1};
+    VIE_TRY(fft_lines<C>(zh, z + base, lo, *B.fx, +1, 1.0 / n, BoxBufs<C>::tmp(B), st));
+  }
+  return VIE_OK;
+}
+
+template vie_status precond_apply<float2>(vie_plan_s*, const float2*, float2*, cudaStream_t);
+template vie_status precond_apply<double2>(vie_plan_s*, const double2*, double2*, cudaStream_t);
+
+}  // namespace vie

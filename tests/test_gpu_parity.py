@@ -1,0 +1,182 @@
+"""GPU parity: libvie (through its C ABI) against the CPU oracle on the same
+seeded inputs.
+
+Tolerances: the complex-FP64 matvec matches to 1e-12 relative (element-wise
+against the largest entry, and in norm); the FP64 preconditioner apply to
+1e-11 (LU + explicit inverse vs. LU solves, condition numbers of D_f ~ 1e2);
+complex-FP32 paths to the single-precision rounding of an FFT chain (2e-5)
+and of the FP32 block inverse (1e-4); solutions to 1e-6 relative error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import cuda_or_fail, maxerr, relerr
+from oracle import operator as op
+from oracle import precond as pc
+from oracle import solve as osolve
+from paper_1903_07884_gb300 import inputs, vie
+from paper_1903_07884_gb300.solver import Plan, make_opts, to_device
+
+pytestmark = pytest.mark.gpu
+
+K0 = 2 * math.pi / 1.55
+
+
+def _oracle_matvec(nx, ny, nz, h, k0, eps_bg, eps, x):
+    M = op.material(eps, eps_bg)
+    k = op.background_k(k0, eps_bg)
+    spec = op.generator_spectra(nx, ny, nz, h, k)
+    return op.fft_matvec(x, M, spec)
+
+
+@pytest.mark.parametrize("shape,eps_bg", [((1, 1, 1), 1.0), ((2, 1, 1), 1.0), ((3, 2, 2), 2.085), ((5, 3, 2), 1.0),
+                                          ((7, 4, 3), 2.085), ((37, 5, 3), 1.0), ((64, 8, 4), 1.0),
+                                          ((33, 12, 2), 2.085)])
+def test_matvec_fp64_matches_oracle(shape, eps_bg):
+    torch = cuda_or_fail()
+    nx, ny, nz = shape
+    h = 0.05
+    eps = inputs.random_permittivity(nz, ny, nx, seed=nx * 7 + ny)
+    x = inputs.random_field((3, nz, ny, nx), seed=3 + nx)
+    ref = _oracle_matvec(nx, ny, nz, h, K0, eps_bg, eps, x)
+    plan = Plan(nx, ny, nz, h, K0, eps_bg, make_opts(precision=vie.VIE_FP64, precond=vie.VIE_PREC_NONE))
+    plan.set_permittivity(eps)
+    y = plan.matvec(to_device(x), vie.VIE_FP64).cpu().numpy()
+    plan.close()
+    assert maxerr(y, ref) <= 1e-12
+    assert relerr(y, ref) <= 1e-12
+    if nx * ny * nz <= 120:   # brute force against the dense matrix too
+        A = op.dense_matrix(nx, ny, nz, h, op.background_k(K0, eps_bg), op.material(eps, eps_bg))
+        assert relerr(y, op.dense_matvec(A, x)) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4)])
+def test_matvec_mixed_matches_oracle(shape):
+    cuda_or_fail()
+    nx, ny, nz = shape
+    eps = inputs.random_permittivity(nz, ny, nx, seed=11)
+    x = inputs.random_field((3, nz, ny, nx), seed=12)
+    ref = _oracle_matvec(nx, ny, nz, 0.025, K0, 1.0, eps, x)
+    plan = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    plan.set_permittivity(eps)
+    y = plan.matvec(to_device(x), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    assert relerr(y, ref) <= 2e-5
+
+
+def test_matvec_long_guide_full_size():
+    """1024x16x8 long straight guide: element-wise against the oracle."""
+    cuda_or_fail()
+    p = inputs.workload_long_straight()
+    x = inputs.random_field((3, p.nz, p.ny, p.nx), seed=5)
+    ref = _oracle_matvec(p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, p.eps, x)
+    plan = Plan.for_problem(p, precision=vie.VIE_FP64, precond=vie.VIE_PREC_NONE)
+    plan.set_permittivity(p.eps)
+    y64 = plan.matvec(to_device(x), vie.VIE_FP64).cpu().numpy()
+    y32 = plan.matvec(to_device(x), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    assert maxerr(y64, ref) <= 1e-12
+    assert relerr(y32, ref) <= 2e-5
+
+
+def test_matvec_bragg_full_size_sampled_rows():
+    """4096x24x8 Bragg grating (unfused x pass): 24 sampled outputs against
+    rows of A evaluated one by one from the generator definition."""
+    cuda_or_fail()
+    p = inputs.workload_bragg()
+    x = inputs.random_field((3, p.nz, p.ny, p.nx), seed=6)
+    plan = Plan.for_problem(p, precision=vie.VIE_FP64, precond=vie.VIE_PREC_NONE)
+    plan.set_permittivity(p.eps)
+    y = plan.matvec(to_device(x), vie.VIE_FP64).cpu().numpy().ravel()
+    plan.close()
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    rng = np.random.default_rng(0)
+    n3 = 3 * p.n_vox
+    rows = list(rng.integers(0, n3, size=20)) + [0, n3 - 1, p.n_vox, 2 * p.n_vox + 12345]
+    xv = x.ravel()
+    for r in rows:
+        ref = op.matrix_row(int(r), p.nx, p.ny, p.nz, p.h, k, M) @ xv
+        scale = max(abs(ref), np.abs(xv).max())
+        assert abs(y[r] - ref) <= 1e-12 * scale * 10
+
+
+def _precond_case(name):
+    if name == "straight_full":
+        p = inputs.straight_guide(40, 4, 2, 0.05, 1.55, absorber=4)
+        return p, 0.0, 3
+    if name == "small_reduced":
+        return inputs.workload_small_straight(), 1e-3, 3
+    if name == "prime_nx_bluestein":
+        return inputs.straight_guide(37, 3, 2, 0.05, 1.55, absorber=3), 0.0, 2
+    if name == "bragg_boxes_mode":
+        return inputs.bragg_grating(96, 12, 4, 0.025, 1.55, wide=8, narrow=6, period=16), 1e-3, 1
+    if name == "coupler_boxes":
+        return inputs.directional_coupler(64, 0.025, 1.55, ny=24, nz=4, core_w=8, gap=4, margin=2), 0.0, 3
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "prime_nx_bluestein", "bragg_boxes_mode",
+                                  "coupler_boxes"])
+def test_precond_fp64_matches_oracle(name):
+    cuda_or_fail()
+    p, tau, variant = _precond_case(name)
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, p.boxes, variant, tau)
+    r = inputs.random_field((3, p.nz, p.ny, p.nx), seed=21)
+    ref = P.apply(r)
+    plan = Plan.for_problem(p, precision=vie.VIE_FP64, reduce_tol=tau, homog=variant)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    z = plan.precond(to_device(r), vie.VIE_FP64).cpu().numpy()
+    plan.close()
+    assert relerr(z, ref) <= 1e-11
+    assert maxerr(z, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode"])
+def test_precond_mixed_matches_oracle(name):
+    cuda_or_fail()
+    p, tau, variant = _precond_case(name)
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, p.boxes, variant, tau)
+    r = inputs.random_field((3, p.nz, p.ny, p.nx), seed=22)
+    ref = P.apply(r)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=tau, homog=variant)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    z = plan.precond(to_device(r), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    assert relerr(z, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(vie.VIE_FP64, 1e-11, 1e-7), (vie.VIE_MIXED, 1e-10, 1e-6)])
+def test_solve_small_straight_matches_dense_lu(precision, tol, bound):
+    """64x8x4 bar with absorbers: GPU solution against the oracle's direct LU."""
+    cuda_or_fail()
+    p = inputs.workload_small_straight()
+    ref = osolve.dense_solve(p)
+    plan = Plan.for_problem(p, precision=precision, tol=tol)
+    plan.set_permittivity(p.eps)
+    w, info = plan.solve(p.e_inc)
+    plan.close()
+    assert info["relres"] <= tol
+    assert relerr(w.cpu().numpy(), ref) <= bound
+
+
+def test_solve_tiny_cases_match_dense_lu():
+    cuda_or_fail()
+    for p in (inputs.straight_guide(1, 1, 1, 0.05, 1.55, absorber=0),
+              inputs.straight_guide(9, 2, 1, 0.05, 1.55, absorber=2),
+              inputs.directional_coupler(12, 0.025, 1.55, ny=12, nz=2, core_w=3, gap=2, margin=2)):
+        ref = osolve.dense_solve(p)
+        for prec in (vie.VIE_FP64, vie.VIE_MIXED):
+            plan = Plan.for_problem(p, precision=prec, tol=1e-11, reduce_tol=0.0)
+            plan.set_permittivity(p.eps)
+            w, info = plan.solve(p.e_inc)
+            plan.close()
+            assert relerr(w.cpu().numpy(), ref) <= 1e-6, (p.name, prec, info)
