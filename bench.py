@@ -1,0 +1,457 @@
+#!/usr/bin/env python3
+"""Benchmark: circulant-preconditioned voxel VIE solves on GB300.
+
+One step = one complete solve of the workload through the libvie C ABI:
+set the permittivity (material operator M), build the block-diagonal
+Chan-Olkin preconditioner (Chan eigenvalues, block assembly, reduction, FP64
+LU, complex-FP32 inverse), and run complex-FP32 GMRES(50) inside FP64
+iterative refinement to the FP64 relative residual 1e-9.
+
+Default workload: the 1024x16x8 long straight silicon wire (h = 0.025 um,
+lambda = 1.55 um, 10% absorbers).  N > 1 GPUs run independent replicas (one
+solve per rank per step, no collective on the data path).
+
+Printed JSON: value = solves/s over all ranks (device time, inputs resident),
+e2e = the same through vie_solve_host with host buffers (copies timed),
+fp64_gpu = the plain FP64 GPU solver on the same problem, roofline = the
+dominant kernel of the solve against the measured peak, cpu_baseline = the
+CPU oracle on a bounded sample scaled to one solve.
+
+--impl reference times the CPU oracle alone (bounded samples, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VIE solves/s at 1e-6 rel. err (mixed vs FP64 GPU); matvec HBM GB/s; p50/p99 ms"
+UNIT = "solves/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP64_PEAK_TFLOPS = 1.196      # DFMA probe on this machine's GB300 (152 SMs at 2.07 GHz)
+FP32_PEAK_TFLOPS = 69.94      # FFMA probe, same run
+
+
+def workload(name):
+    from paper_1903_07884_gb300 import inputs
+    if name == "long_straight":
+        return inputs.workload_long_straight(), "long_straight_1024x16x8"
+    if name == "small_straight":
+        return inputs.workload_small_straight(), "small_straight_64x8x4"
+    if name == "bragg":
+        return inputs.workload_bragg(), "bragg_4096x24x8_2boxes"
+    if name == "coupler":
+        return inputs.workload_coupler(), "coupler_2048x48x8_2boxes"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of the kernels that can dominate a solve
+# ---------------------------------------------------------------------------
+def algorithmic(kernel: str, p, plan_meta: dict):
+    """(kind, amount per launch, unit) or None.  Complex FP32 = 8 bytes."""
+    nx, ny, nz = p.nx, p.ny, p.nz
+    N = nx * ny * nz
+    L, Py, Pz = 2 * _smooth(nx), 2 * _smooth(ny), 2 * _smooth(nz)
+    T = 3 * nx * Py * Pz               # yz-transformed intermediate (complex)
+    oct_ = 6 * (L // 2 + 1) * (Py // 2 + 1) * (Pz // 2 + 1)
+    c = 8
+    if kernel == "mv_yz_fwd":
+        return "hbm", c * (3 * N + T)
+    if kernel == "mv_x":
+        return "hbm", c * (2 * T + oct_)
+    if kernel == "mv_yz_inv":
+        return "hbm", c * (T + 3 * N + N + 3 * N)
+    if kernel == "block_lu":
+        m, nblk = plan_meta["m"], plan_meta["nblk"]
+        return "alu", nblk * (8.0 / 3.0) * m ** 3     # complex LU: m^3/3 complex multiply-adds
+    if kernel == "block_gemv":
+        m, nh = plan_meta["m"], plan_meta["nhalf"]
+        return "hbm", c * nh * m * m
+    return None
+
+
+def _smooth(n):
+    def ok(v):
+        for q in (2, 3, 5, 7):
+            while v % q == 0:
+                v //= q
+        return v == 1
+    while not ok(n):
+        n += 1
+    return n
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_iterations(wname: str, tol: float):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if os.path.exists(path):
+        d = json.load(open(path)).get(wname, {}).get(f"{tol:g}")
+        if d:
+            return int(d["iters"]), "oracle GMRES count from tests/golden/oracle_iterations.json"
+    return None, None
+
+
+class OracleSample:
+    """Times the oracle's setup (generator spectra + full preconditioner
+    build) once and its per-iteration work (FFT matvec, preconditioner apply,
+    modified Gram-Schmidt against a 25-vector basis) on a few iterations."""
+
+    def __init__(self, p):
+        import numpy as np
+        from oracle import operator as op
+        from oracle import precond as pc
+        self.np = np
+        self.p = p
+        t0 = time.perf_counter()
+        self.k = op.background_k(p.k0, p.eps_bg)
+        self.M = op.material(p.eps, p.eps_bg)
+        self.b = op.rhs(p.eps, p.eps_bg, p.e_inc)
+        self.spec = op.generator_spectra(p.nx, p.ny, p.nz, p.h, self.k)
+        self.P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, self.k, self.M, p.boxes, p.homog, 1e-3)
+        self.t_setup = time.perf_counter() - t0
+        rng = np.random.default_rng(0)
+        self.V = rng.standard_normal((25, self.b.size)) + 1j * rng.standard_normal((25, self.b.size))
+
+    def iteration(self) -> float:
+        from oracle import operator as op
+        np = self.np
+        t0 = time.perf_counter()
+        z = self.P.apply(self.b)
+        w = op.fft_matvec(z, self.M, self.spec).ravel()
+        for i in range(self.V.shape[0]):
+            h = np.vdot(self.V[i], w)
+            w = w - h * self.V[i]
+        return time.perf_counter() - t0
+
+    def residual(self, w_gpu) -> float:
+        from oracle import operator as op
+        np = self.np
+        r = self.b - op.fft_matvec(w_gpu, self.M, self.spec)
+        return float(np.linalg.norm(r) / np.linalg.norm(self.b))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle alone
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p, wname = workload(args.workload)
+    iters, src = oracle_iterations(wname, args.tol)
+    S = OracleSample(p)
+    for _ in range(args.warmup):
+        S.iteration()
+    ts = [S.iteration() for _ in range(args.steps)]
+    t_it = statistics.mean(ts)
+    if iters is None:
+        iters, src = 400, "assumed 400 iterations (no stored oracle count)"
+    t_solve = S.t_setup + iters * t_it
+    value = 1.0 / t_solve
+    cores = cpu_cores()
+    sample = (f"oracle setup (spectra + preconditioner build, {S.t_setup:.2f} s, once) + {args.steps} timed "
+              f"iteration samples (FFT matvec + preconditioner apply + 25-vector MGS, mean {t_it:.3f} s); one solve "
+              f"= setup + {iters} iterations ({src})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_it, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": wname, "precision": "fp64 (CPU oracle)", "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1903_07884_gb300 import vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p, wname = workload(args.workload)
+    N = p.n_vox
+    eps_d = to_device(p.eps, dev)
+    e_d = to_device(p.e_inc, dev)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, tol=args.tol)
+
+    def step():
+        plan.set_permittivity(eps_d)
+        plan.build()
+        return plan.solve(e_d)
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = vie.vie_kernel_launches()
+    times, infos = [], []
+    w = None
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("bench_step")
+        e0.record(plan.stream)
+        w, info = step()
+        e1.record(plan.stream)
+        torch.cuda.nvtx.range_pop()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier()
+    launches = vie.vie_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    w_mixed = w.cpu().numpy()
+
+    # plain FP64 GPU method on the same problem, same tolerance
+    plan64 = Plan.for_problem(p, precision=vie.VIE_FP64, tol=args.tol)
+    t64 = []
+    w64 = None
+    info64 = None
+    for k in range(1 + args.fp64_steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(plan64.stream)
+        plan64.set_permittivity(eps_d)
+        plan64.build()
+        w64, info64 = plan64.solve(e_d)
+        e1.record(plan64.stream)
+        e1.synchronize()
+        if k > 0:
+            t64.append(e0.elapsed_time(e1))
+    w64 = w64.cpu().numpy()
+    plan64.close()
+    diff = float(np.linalg.norm(w_mixed - w64) / np.linalg.norm(w64))
+
+    # end to end through the host-buffer entry point (copies timed)
+    eps_h = torch.from_numpy(np.ascontiguousarray(p.eps)).pin_memory()
+    e_h = torch.from_numpy(np.ascontiguousarray(p.e_inc)).pin_memory()
+    w_h = torch.empty(p.e_inc.shape, dtype=torch.complex128).pin_memory()
+    te = []
+    for k in range(1 + max(1, args.steps // 2)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(plan.stream)
+        vie.vie_solve_host(plan.handle, eps_h.data_ptr(), e_h.data_ptr(), w_h.data_ptr())
+        e1.record(plan.stream)
+        e1.synchronize()
+        if k > 0:
+            te.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(te)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # per-kernel device time of one profiled solve (eager launches)
+    vie.vie_profile_reset()
+    vie.vie_profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    vie.vie_profile_enable(False)
+    table = vie.profile_table()
+    vie.vie_profile_reset()
+    total_prof = sum(t for _, t in table.values())
+    top = sorted(table.items(), key=lambda kv: -kv[1][1])
+    pk, pk_src = peaks()
+    meta = plan_meta(p, infos[-1])
+    roof = None
+    for name, (cnt, tot) in top:
+        a = algorithmic(name, p, meta)
+        if a is None:
+            continue
+        kind, amount = a
+        avg_ms = tot / cnt
+        if kind == "hbm":
+            ach = amount / (avg_ms * 1e-3) / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / pk["hbm_gbs"], "traffic": None, "share": tot / total_prof,
+                    "avg_launch_ms": avg_ms, "launches": cnt, "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)"}
+        else:
+            ach = amount / (avg_ms * 1e-3) / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": tot / total_prof,
+                    "avg_launch_ms": avg_ms, "launches": cnt,
+                    "peak_source": "FP64 FMA probe (8 independent DFMA chains x 8 warps x 152 SMs)"}
+        break
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": wname, "grid": [p.nx, p.ny, p.nz], "h_um": p.h, "lambda_um": p.wavelength,
+                       "precision": "mixed: c64 GMRES(50) in FP64 iterative refinement", "tol": args.tol,
+                       "preconditioner": "1-level Chan-Olkin, real-mean homogenised, reduction tau=1e-3",
+                       "l2": "512 MB buffer written between timed steps (outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "iters": {"inner": infos[-1]["iters_inner"], "outer": infos[-1]["iters_outer"]},
+            "relres_fp64": infos[-1]["relres"], "kept_fraction": infos[-1]["kept_fraction"],
+            "precond_bytes": infos[-1]["precond_bytes"],
+            "fp64_gpu": {"value": 1000.0 / statistics.mean(t64) if t64 else None, "unit": UNIT,
+                         "ms_per_solve": statistics.mean(t64) if t64 else None,
+                         "iters": info64["iters_inner"], "relres_fp64": info64["relres"],
+                         "rel_diff_mixed_vs_fp64": diff},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
+                    "h2d_bytes_per_step": int(16 * N + 16 * 3 * N), "d2h_bytes_per_step": int(16 * 3 * N)},
+            "roofline": roof,
+            "profile_ms": {k: round(v[1], 4) for k, v in top[:12]}}
+    plan.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S = OracleSample(p)
+        ts = [S.iteration() for _ in range(3)]
+        iters, src = oracle_iterations(wname, args.tol)
+        if iters is None:
+            iters, src = infos[-1]["iters_inner"], "iteration count of the GPU solve"
+        t_solve = S.t_setup + iters * statistics.mean(ts)
+        line["cpu_baseline"] = {
+            "value": 1.0 / t_solve, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": (f"oracle setup {S.t_setup:.2f} s (spectra + preconditioner build) + 3 iteration samples "
+                       f"(mean {statistics.mean(ts):.3f} s); one solve = setup + {iters} iterations ({src})")}
+        line["accuracy"] = {"oracle_relres_of_mixed_solution": S.residual(w_mixed),
+                            "oracle_relres_of_fp64_solution": S.residual(w64)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def plan_meta(p, info):
+    """Block sizes of the preconditioner for the work formulas: every box of
+    the workloads has the same cross-section, so the stored complex-FP32
+    inverses give the blocks per box (one LU launch per box)."""
+    boxes = p.boxes or [(0, 0, 0, p.nx, p.ny, p.nz)]
+    m = 3 * boxes[0][4] * boxes[0][5]
+    nblk = info["precond_bytes"] / (8.0 * m * m) / len(boxes)
+    nkept = info["kept_fraction"] * sum(b[3] for b in boxes) / len(boxes)
+    return {"m": m, "nblk": nblk, "nhalf": max(1.0, (nkept + 1) / 2.0)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gvie", choices=["gvie", "reference"])
+    ap.add_argument("--workload", default="long_straight")
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

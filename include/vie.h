@@ -195,8 +195,22 @@ void vie_server_destroy(vie_server_t srv);
 const char* vie_last_error(void);
 
 /* Number of kernels this library has launched in this process (all plans);
- * used to report launch counts. */
+ * used to report launch counts.  Launches inside a replayed CUDA graph are
+ * counted once per replay and kernel. */
 int64_t vie_kernel_launches(void);
+
+/* Per-kernel device timing, a benchmark and test hook.  While enabled
+ * (on != 0), solves launch their Arnoldi steps eagerly instead of through a
+ * CUDA graph and every library kernel launch is bracketed by two CUDA events
+ * on its stream.  vie_profile_query sums, for one kernel name (e.g. "mv_x",
+ * "block_lu", "arnoldi_update"), the launches recorded since the last
+ * vie_profile_reset and their total device time in ms (it synchronises on
+ * the recorded events).  vie_profile_kernels writes up to cap distinct
+ * recorded names into names (static strings) and returns how many exist. */
+void vie_profile_enable(int on);
+void vie_profile_reset(void);
+vie_status vie_profile_query(const char* kernel, int64_t* launches, double* total_ms);
+int vie_profile_kernels(const char** names, int cap);
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "prof.h"
 
 namespace vie {
 
@@ -99,6 +100,33 @@ static bool boxes_valid(int nx, int ny, int nz, const std::vector<vie_box>& bs) 
 
 static int embed_len(int n) { return 2 * fft_next_smooth(n); }
 
+std::atomic<int> g_prof_on{0};
+struct ProfRec { const char* name; cudaEvent_t e0, e1; };
+static std::mutex g_prof_mu;
+static std::vector<ProfRec>* g_prof = nullptr;
+static std::vector<cudaEvent_t>* g_ev_pool = nullptr;
+
+static cudaEvent_t prof_event() {
+  if (!g_ev_pool) g_ev_pool = new std::vector<cudaEvent_t>();
+  if (!g_ev_pool->empty()) { cudaEvent_t e = g_ev_pool->back(); g_ev_pool->pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_record(const char* name, cudaStream_t st, cudaEvent_t* e0, cudaEvent_t* e1, bool begin) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (begin) {
+    *e0 = prof_event();
+    cudaEventRecord(*e0, st);
+  } else {
+    *e1 = prof_event();
+    cudaEventRecord(*e1, st);
+    if (!g_prof) g_prof = new std::vector<ProfRec>();
+    g_prof->push_back(ProfRec{name, *e0, *e1});
+  }
+}
+
 }  // namespace vie
 
 using namespace vie;
@@ -121,6 +149,53 @@ void vie_default_opts(vie_opts* o) {
 }
 
 const char* vie_last_error(void) { return g_err; }
+
+void vie_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+void vie_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof) return;
+  for (auto& r : *g_prof) {
+    cudaEventSynchronize(r.e1);
+    if (!g_ev_pool) g_ev_pool = new std::vector<cudaEvent_t>();
+    g_ev_pool->push_back(r.e0);
+    g_ev_pool->push_back(r.e1);
+  }
+  g_prof->clear();
+}
+
+vie_status vie_profile_query(const char* kernel, int64_t* launches, double* total_ms) {
+  if (!kernel || !launches || !total_ms) { set_error("vie_profile_query: NULL argument"); return VIE_EINVAL; }
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int64_t n = 0;
+  double t = 0;
+  if (g_prof) {
+    for (auto& r : *g_prof) {
+      if (strcmp(r.name, kernel) != 0) continue;
+      if (cudaEventSynchronize(r.e1) != cudaSuccess) { set_error("vie_profile_query: event failed"); return VIE_ECUDA; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, r.e0, r.e1);
+      t += ms;
+      ++n;
+    }
+  }
+  *launches = n;
+  *total_ms = t;
+  return VIE_OK;
+}
+
+int vie_profile_kernels(const char** names, int cap) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::vector<const char*> seen;
+  if (g_prof)
+    for (auto& r : *g_prof) {
+      bool dup = false;
+      for (const char* q : seen) if (strcmp(q, r.name) == 0) { dup = true; break; }
+      if (!dup) seen.push_back(r.name);
+    }
+  for (int i = 0; i < (int)seen.size() && i < cap; ++i) names[i] = seen[i];
+  return (int)seen.size();
+}
 
 int64_t vie_kernel_launches(void) { return (int64_t)launches_total(); }
 

@@ -17,6 +17,7 @@
 #include <chrono>
 
 #include "internal.h"
+#include "prof.h"
 
 namespace vie {
 
@@ -476,13 +477,13 @@ static vie_status enqueue_step(vie_plan_s* P) {
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
   for (int pass = 0; pass < 2; ++pass) {
-    k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part);
-    k_reduce_h<<<1, 128, 0, st>>>(part, s, NPART, pass);
-    k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1);
+    { Prof pf_("arnoldi_dot", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part); }
+    { Prof pf_("arnoldi_reduce", st); k_reduce_h<<<1, 128, 0, st>>>(part, s, NPART, pass); }
+    { Prof pf_("arnoldi_update", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1); }
     count_launch(3);
   }
-  k_givens<<<1, 32, 0, st>>>(s, part, NPART);
-  k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s);
+  { Prof pf_("givens", st); k_givens<<<1, 32, 0, st>>>(s, part, NPART); }
+  { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s); }
   count_launch(2);
   VIE_CHECK_LAUNCH();
   return VIE_OK;
@@ -528,7 +529,7 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     k_cycle_v0<C><<<grid_for(n3), 256, 0, st>>>(rwork, V, u, n3, s);
     count_launch(3);
     VIE_CHECK_LAUNCH();
-    if (!gexec) {
+    if (!gexec && !prof_enabled()) {
       // one Arnoldi step as a graph: its kernels read j and the stop flag
       // from device memory, so the same graph serves every step
       // capture on a private stream (the plan stream may be the legacy
@@ -555,8 +556,12 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     const int cyc = std::min(K.restart, max_iter - total);
     while (!done && steps_cycle < cyc) {
       const int chunk = std::min(4, cyc - steps_cycle);
-      for (int c = 0; c < chunk; ++c) VIE_CUDA(cudaGraphLaunch(gexec, st));
-      count_launch(chunk * step_kernels(P));
+      if (prof_enabled()) {
+        for (int c = 0; c < chunk; ++c) VIE_TRY(enqueue_step<C>(P));
+      } else {
+        for (int c = 0; c < chunk; ++c) VIE_CUDA(cudaGraphLaunch(gexec, st));
+        count_launch(chunk * step_kernels(P));
+      }
       steps_cycle += chunk;
       VIE_CUDA(cudaMemcpyAsync(K.hflag, &s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
       VIE_CUDA(cudaMemcpyAsync(K.hflag + 1, &s->iters, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -22,6 +22,7 @@
 
 #include "greens.cuh"
 #include "internal.h"
+#include "prof.h"
 
 namespace vie {
 
@@ -607,6 +608,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   {
     const long long total = (long long)nl * n;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    Prof pf_("chan_coeffs", st);
     k_chan_coeffs<<<grid, 256, 0, st>>>(coef.as<double2>(), bd, P->h, P->kb, self);
     count_launch();
     VIE_CHECK_LAUNCH();
@@ -651,6 +653,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   {
     const long long total = (long long)mm * B.nblk;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+    Prof pf_("block_assemble", st);
     k_block_assemble<<<grid, 256, 0, st>>>(LU.as<double2>(), B.lam.as<double2>(), B.Mt.as<double2>(),
                                            B.blkf.as<int>(), bd, B.nblk);
     count_launch();
@@ -660,6 +663,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   {
     const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
     VIE_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    Prof pf_("block_lu", st);
     k_block_lu<<<B.nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, info.as<int>());
     count_launch();
     VIE_CHECK_LAUNCH();
@@ -670,7 +674,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
     const size_t smem = sizeof(float2) * (size_t)m * CB;
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB);
+    { Prof pf_("block_inv_c64", st);
+      k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB); }
     count_launch();
     VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
@@ -681,7 +686,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
     const size_t smem = sizeof(double2) * (size_t)m * CB;
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB);
+    { Prof pf_("block_inv_c128", st);
+      k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB); }
     count_launch();
     VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat128.alloc(sizeof(double2) * (size_t)n * m));
@@ -759,6 +765,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
     // kept blocks (S1 pairs)
     if (B.nhalf > 0) {
       const size_t smem = sizeof(C) * 2 * m;
+      Prof pf_("block_gemv", st);
       k_block_gemv<C><<<B.nhalf, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, n, nyb * nzb);
       count_launch();
       VIE_CHECK_LAUNCH();
@@ -769,6 +776,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
       const size_t smem = sizeof(C) * FT * m;
       auto kern = k_rep_gemm<C, FT>;
       if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      Prof pf_("rep_gemm", st);
       kern<<<ceil_div(B.ndisc, FT), 256, smem, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m);
       count_launch();
       VIE_CHECK_LAUNCH();

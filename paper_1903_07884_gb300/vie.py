@@ -81,6 +81,11 @@ _SIGS = {
     "vie_server_destroy": (None, [ctypes.c_void_p]),
     "vie_last_error": (ctypes.c_char_p, []),
     "vie_kernel_launches": (ctypes.c_int64, []),
+    "vie_profile_enable": (None, [ctypes.c_int]),
+    "vie_profile_reset": (None, []),
+    "vie_profile_query": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "vie_profile_kernels": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
 }
 
 
@@ -222,3 +227,30 @@ def vie_server_destroy(srv) -> None:
 
 def vie_kernel_launches() -> int:
     return lib().vie_kernel_launches()
+
+
+def vie_profile_enable(on: bool) -> None:
+    lib().vie_profile_enable(1 if on else 0)
+
+
+def vie_profile_reset() -> None:
+    lib().vie_profile_reset()
+
+
+def vie_profile_query(kernel: str):
+    n = ctypes.c_int64()
+    t = ctypes.c_double()
+    check(lib().vie_profile_query(kernel.encode(), ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def vie_profile_kernels():
+    cap = 64
+    arr = (ctypes.c_char_p * cap)()
+    n = lib().vie_profile_kernels(arr, cap)
+    return [arr[i].decode() for i in range(min(n, cap))]
+
+
+def profile_table() -> dict:
+    """{kernel: (launches, total_ms)} for every kernel recorded since the last reset."""
+    return {k: vie_profile_query(k) for k in vie_profile_kernels()}
