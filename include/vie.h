@@ -191,6 +191,28 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts);
 
 void vie_server_destroy(vie_server_t srv);
 
+/* Allocation-free matvec.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory at all (a host
+ * framework that owns every byte of the GPU through its own pool, a
+ * real-time loop with a fixed budget), and so cannot create a plan.
+ * Computes the same y = x - M (x + G x) in complex FP64 as
+ * vie_matvec(plan, x, y, VIE_FP64) for a plan with this grid, voxel size,
+ * wavenumber, background and permittivity, from the caller's buffers only:
+ * eps_dev [nz][ny][nx], x_dev and y_dev [3][nz][ny][nx] (device, double2;
+ * x and y may not alias), cuda_stream a cudaStream_t or NULL.  Every
+ * temporary lives in one file-scope device array of 64 MiB inside libvie
+ * (held by each GPU from the first call -- or from context creation under
+ * eager module loading -- until the process exits); grids that need more,
+ * or whose x-embedding exceeds 4266 points (nx > 2130) or whose Py*Pz
+ * exceeds 4096, are rejected with VIE_EINVAL and a message.  The first call
+ * on a device resolves the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * array: calls whose GPU work overlaps (other streams or threads) race and
+ * corrupt each other's results.  Calls no cudaMalloc / cudaFree.
+ * Asynchronous on cuda_stream. */
+vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double eps_bg, const void* eps_dev,
+                             const void* x_dev, void* y_dev, void* cuda_stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* vie_last_error(void);
 

@@ -124,3 +124,40 @@ vie_status set_material(vie_plan_s* P, const double2* eps) {
 }
 
 }  // namespace vie
+
+namespace vie {
+
+// Launch wrappers over explicit buffers (used by the allocation-free matvec
+// entry point); the plan path above is unchanged.
+vie_status launch_gen_padded(double2* out, int c, const MvDims& d, double h, double kb, cudaStream_t st) {
+  const long long Pn = (long long)d.L * d.Py * d.Pz;
+  const int threads = 256;
+  const int grid = (int)std::min<long long>((Pn + threads - 1) / threads, 152LL * 16);
+  k_gen_padded<<<grid, threads, 0, st>>>(out, c, d, h, kb, self_term_value(h, kb));
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+vie_status launch_octant(const double2* full, double2* s128, float2* s64, int c, const MvDims& d, cudaStream_t st) {
+  const long long Q = (long long)d.Lh * d.Pyh * d.Pzh;
+  const long long Pn = (long long)d.L * d.Py * d.Pz;
+  const int threads = 256;
+  const int grid = (int)std::min<long long>((Q + threads - 1) / threads, 152LL * 16);
+  k_octant<<<grid, threads, 0, st>>>(full, s128, s64, c, d, 1.0 / (double)Pn);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+vie_status launch_material(const double2* eps, double2* M128, float2* M64, long long n, double eps_bg,
+                           cudaStream_t st) {
+  const int threads = 256;
+  const int grid = (int)std::min<long long>((n + threads - 1) / threads, 152LL * 8);
+  k_material<<<grid, threads, 0, st>>>(eps, M128, M64, n, eps_bg);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+}  // namespace vie

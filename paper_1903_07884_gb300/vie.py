@@ -79,6 +79,9 @@ _SIGS = {
     "vie_server_reserved_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "vie_estimate_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vie_opts)]),
     "vie_server_destroy": (None, [ctypes.c_void_p]),
+    "vie_matvec_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "vie_last_error": (ctypes.c_char_p, []),
     "vie_kernel_launches": (ctypes.c_int64, []),
     "vie_profile_enable": (None, [ctypes.c_int]),
@@ -223,6 +226,13 @@ def vie_estimate_bytes(nx, ny, nz, opts=None) -> int:
 
 def vie_server_destroy(srv) -> None:
     lib().vie_server_destroy(srv)
+
+
+def vie_matvec_static(nx, ny, nz, h, k0, eps_bg, eps_ptr: int, x_ptr: int, y_ptr: int, stream: int = 0) -> int:
+    """Allocation-free complex-FP64 matvec (all scratch in a fixed array inside
+    libvie); returns the status code unchanged."""
+    return lib().vie_matvec_static(nx, ny, nz, h, k0, eps_bg, ctypes.c_void_p(eps_ptr), ctypes.c_void_p(x_ptr),
+                                   ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream))
 
 
 def vie_kernel_launches() -> int:
