@@ -114,25 +114,34 @@ class ClockSampler:
 # algorithmic work per launch of the kernels that can dominate a solve
 # ---------------------------------------------------------------------------
 def algorithmic(kernel: str, p, plan_meta: dict):
-    """(kind, amount per launch, unit) or None.  Complex FP32 = 8 bytes."""
+    """(kind, amount per launch) or None, for the complex-FP32 kernels of the
+    solve (8 bytes per complex value).  Byte counts are the minimum each
+    kernel must move; the matvec intermediate T is the yz-transformed field
+    [3][Py][Pz][nx] of the three-pass scheme."""
     nx, ny, nz = p.nx, p.ny, p.nz
     N = nx * ny * nz
+    n3 = 3 * N
     L, Py, Pz = 2 * _smooth(nx), 2 * _smooth(ny), 2 * _smooth(nz)
-    T = 3 * nx * Py * Pz               # yz-transformed intermediate (complex)
+    T = 3 * nx * Py * Pz
     oct_ = 6 * (L // 2 + 1) * (Py // 2 + 1) * (Pz // 2 + 1)
     c = 8
-    if kernel == "mv_yz_fwd":
-        return "hbm", c * (3 * N + T)
-    if kernel == "mv_x":
+    jbar = plan_meta.get("mean_j1", 25.5)          # mean number of basis vectors read per launch
+    if kernel == "mv_yz_fwd_c64":
+        return "hbm", c * (n3 + T)
+    if kernel == "mv_x_c64":
         return "hbm", c * (2 * T + oct_)
-    if kernel == "mv_yz_inv":
-        return "hbm", c * (T + 3 * N + N + 3 * N)
+    if kernel == "mv_yz_inv_c64":
+        return "hbm", c * (T + n3 + N + n3)
+    if kernel == "arnoldi_dot_c64":
+        return "hbm", c * (jbar + 1) * n3
+    if kernel == "arnoldi_update_c64":
+        return "hbm", c * (jbar + 2) * n3
+    if kernel == "block_gemv_c64":
+        m, nh = plan_meta["m"], plan_meta["nhalf"]
+        return "hbm", c * nh * m * m
     if kernel == "block_lu":
         m, nblk = plan_meta["m"], plan_meta["nblk"]
         return "alu", nblk * (8.0 / 3.0) * m ** 3     # complex LU: m^3/3 complex multiply-adds
-    if kernel == "block_gemv":
-        m, nh = plan_meta["m"], plan_meta["nhalf"]
-        return "hbm", c * nh * m * m
     return None
 
 
@@ -434,7 +443,12 @@ def plan_meta(p, info):
     m = 3 * boxes[0][4] * boxes[0][5]
     nblk = info["precond_bytes"] / (8.0 * m * m) / len(boxes)
     nkept = info["kept_fraction"] * sum(b[3] for b in boxes) / len(boxes)
-    return {"m": m, "nblk": nblk, "nhalf": max(1.0, (nkept + 1) / 2.0)}
+    # mean (j + 1) over the Arnoldi steps: every refinement step is one
+    # restart cycle of at most 50 steps
+    its, outer = info["iters_inner"], max(1, info["iters_outer"])
+    per = its / outer
+    mean_j1 = (per + 1) / 2.0
+    return {"m": m, "nblk": nblk, "nhalf": max(1.0, (nkept + 1) / 2.0), "mean_j1": mean_j1}
 
 
 def main():

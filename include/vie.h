@@ -74,7 +74,7 @@ typedef struct {
   int restart;            /* GMRES restart length (default 50)                      */
   double tol;             /* stop at ||b - A w||_2 / ||b||_2 <= tol (FP64 residual) */
   int max_iter;           /* cap on total GMRES iterations (all restarts/refinements)*/
-  double inner_tol;       /* mixed: relative tolerance of each inner c64 GMRES      */
+  double inner_tol;       /* mixed: floor of each inner c64 cycle's relative target */
   int max_refine;         /* mixed: cap on FP64 iterative-refinement steps          */
   int precision;          /* vie_precision                                          */
   int precond;            /* vie_precond_kind                                       */
@@ -97,7 +97,7 @@ typedef struct {
 typedef struct vie_plan_s* vie_plan_t;
 
 /* Fill *opts with the defaults: restart 50, tol 1e-9, max_iter 5000,
- * inner_tol 1e-4, max_refine 20, VIE_MIXED, VIE_PREC_CIRCULANT,
+ * inner_tol 1e-6, max_refine 1000, VIE_MIXED, VIE_PREC_CIRCULANT,
  * VIE_HOM_REALMEAN, reduce_tol 1e-3, whole-grid box. */
 void vie_default_opts(vie_opts* opts);
 
@@ -142,7 +142,10 @@ vie_status vie_precond_apply(vie_plan_t plan, const void* r_dev, void* z_dev, in
 
 /* Solve (I - M N) w = M e_inc (Sec. 2) with right-preconditioned GMRES
  * (restart opts.restart).  VIE_FP64: complex FP64 throughout.  VIE_MIXED:
- * complex FP32 GMRES inside FP64 iterative refinement.  e_inc and w_out are
+ * FP64 iterative refinement whose every step runs one complex-FP32 GMRES
+ * cycle on the scaled FP64 residual (stopped early at the relative target
+ * max(inner_tol, tol ||b|| / (2 ||r||))), so GMRES restarts from FP64
+ * residuals.  e_inc and w_out are
  * device [3][nz][ny][nx] double2.  Builds the preconditioner if needed.
  * info may be NULL.  Synchronises the plan stream. */
 vie_status vie_solve(vie_plan_t plan, const void* e_inc_dev, void* w_out_dev, vie_info* info);

@@ -138,8 +138,8 @@ void vie_default_opts(vie_opts* o) {
   o->restart = 50;
   o->tol = 1e-9;
   o->max_iter = 5000;
-  o->inner_tol = 1e-4;
-  o->max_refine = 20;
+  o->inner_tol = 1e-6;
+  o->max_refine = 1000;
   o->precision = VIE_MIXED;
   o->precond = VIE_PREC_CIRCULANT;
   o->homog = VIE_HOM_REALMEAN;

@@ -223,7 +223,7 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
     auto kern = k_fft_lines<C, ME>;                                                               \
     if (smem > 48 * 1024)                                                                         \
       VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    Prof pf_("fft_lines", st);                                                                    \
+    Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);                                                                    \
     kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode,  \
                                       post2, post2_mode, scale);                                 \
   }

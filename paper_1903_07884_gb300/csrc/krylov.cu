@@ -99,44 +99,88 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
   return t;   // valid in thread 0
 }
 
-// partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j
+// partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j.
+// Each thread accumulates DOT_T columns at once, so one pass over its
+// elements serves DOT_T dot products and one block reduction.
+constexpr int DOT_T = 8;
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
                                                              long long n3, const GmresDev* __restrict__ s,
                                                              double2* __restrict__ partial) {
-  __shared__ double2 sh[32];
+  __shared__ double2 sh[RED_THREADS / 32][DOT_T];
   if (s->done) return;
   const int j = s->j;
   const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
   const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
   using T = typename Acc<C>::T;
-  for (int i = 0; i <= j; ++i) {
-    const C* Vi = V + (long long)i * n3;
-    T ar = 0, ai = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += DOT_T) {
+    T ar[DOT_T], ai[DOT_T];
+#pragma unroll
+    for (int t = 0; t < DOT_T; ++t) { ar[t] = 0; ai[t] = 0; }
+    const int nt = min(DOT_T, j + 1 - i0);
     for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
-      const C v = Vi[e], x = w[e];
-      ar += v.x * x.x + v.y * x.y;
-      ai += v.x * x.y - v.y * x.x;
+      const C x = w[e];
+#pragma unroll
+      for (int t = 0; t < DOT_T; ++t) {
+        if (t < nt) {
+          const C v = V[(long long)(i0 + t) * n3 + e];
+          ar[t] += v.x * x.x + v.y * x.y;
+          ai[t] += v.x * x.y - v.y * x.x;
+        }
+      }
     }
-    const double2 t = block_sum2(make_double2(ar, ai), sh);
-    if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1) + i] = t;
+    // warp sums in the accumulator precision (FP64 throughput is low on
+    // this part), block sums in FP64
+#pragma unroll
+    for (int t = 0; t < DOT_T; ++t) {
+      T xr = ar[t], xi = ai[t];
+      for (int o = 16; o > 0; o >>= 1) {
+        xr += __shfl_xor_sync(0xffffffffu, xr, o);
+        xi += __shfl_xor_sync(0xffffffffu, xi, o);
+      }
+      if (lane == 0) sh[warp][t] = make_double2((double)xr, (double)xi);
+    }
+    __syncthreads();
+    if (threadIdx.x < nt) {
+      double2 acc = make_double2(0, 0);
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { acc.x += sh[w2][threadIdx.x].x; acc.y += sh[w2][threadIdx.x].y; }
+      partial[(long long)blockIdx.x * (RMAX + 1) + i0 + threadIdx.x] = acc;
+    }
+    __syncthreads();
   }
 }
 
-// hc[i] = sum_b partial[b][i]; mode 0: hsum = hc, mode 1: hsum += hc
+// sum of partial[b][i] over b by one warp (fixed order: lane-strided sums,
+// then a butterfly)
+__device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__ partial, int nparts, int i) {
+  const int lane = threadIdx.x & 31;
+  double2 t = make_double2(0, 0);
+  for (int b = lane; b < nparts; b += 32) {
+    const double2 p = partial[(long long)b * (RMAX + 1) + i];
+    t.x += p.x;
+    t.y += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  }
+  return t;
+}
+
+// hc[i] = sum_b partial[b][i]; mode 0: hsum = hc, mode 1: hsum += hc.
+// One warp per coefficient.
 __global__ void k_reduce_h(const double2* __restrict__ partial, GmresDev* __restrict__ s, int nparts, int mode) {
   if (s->done) return;
   const int j = s->j;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    double2 t = make_double2(0, 0);
-    for (int b = 0; b < nparts; ++b) {
-      const double2 p = partial[(long long)b * (RMAX + 1) + i];
-      t.x += p.x;
-      t.y += p.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    const double2 t = warp_sum_partials(partial, nparts, i);
+    if (lane == 0) {
+      s->hc[i] = t;
+      if (mode == 0) s->hsum[i] = t;
+      else { s->hsum[i].x += t.x; s->hsum[i].y += t.y; }
     }
-    s->hc[i] = t;
-    if (mode == 0) s->hsum[i] = t;
-    else { s->hsum[i].x += t.x; s->hsum[i].y += t.y; }
   }
 }
 
@@ -157,7 +201,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V,
   T nrm = 0;
   for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
     C x = w[e];
-    for (int i = 0; i <= j; ++i) {
+    int i = 0;
+    for (; i + 3 <= j; i += 4) {
+      const C v0 = V[(long long)i * n3 + e], v1 = V[(long long)(i + 1) * n3 + e];
+      const C v2 = V[(long long)(i + 2) * n3 + e], v3 = V[(long long)(i + 3) * n3 + e];
+      const C h0 = hcs[i], h1 = hcs[i + 1], h2 = hcs[i + 2], h3 = hcs[i + 3];
+      x.x -= h0.x * v0.x - h0.y * v0.y; x.y -= h0.x * v0.y + h0.y * v0.x;
+      x.x -= h1.x * v1.x - h1.y * v1.y; x.y -= h1.x * v1.y + h1.y * v1.x;
+      x.x -= h2.x * v2.x - h2.y * v2.y; x.y -= h2.x * v2.y + h2.y * v2.x;
+      x.x -= h3.x * v3.x - h3.y * v3.y; x.y -= h3.x * v3.y + h3.y * v3.x;
+    }
+    for (; i <= j; ++i) {
       const C v = V[(long long)i * n3 + e];
       const C h = hcs[i];
       x.x -= h.x * v.x - h.y * v.y;
@@ -167,17 +221,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V,
     nrm += x.x * x.x + x.y * x.y;
   }
   if (want_norm) {
-    const double2 t = block_sum2(make_double2(nrm, 0), sh);
-    if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1)] = t;
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = make_double2((double)nrm, 0.0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2].x;
+      partial[(long long)blockIdx.x * (RMAX + 1)] = make_double2(t, 0.0);
+    }
   }
 }
 
 // Hessenberg column, rotations, residual estimate, stop test
 __global__ void k_givens(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts) {
-  if (threadIdx.x != 0 || s->done) return;
+  if (s->done) return;
+  const double nn = warp_sum_partials(partial, nparts, 0).x;
+  if (threadIdx.x != 0) return;
   const int j = s->j;
-  double nn = 0;
-  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
   const double hn = sqrt(nn);
   double2* col = s->H + (long long)j * (RMAX + 1);
   for (int i = 0; i <= j; ++i) col[i] = s->hsum[i];
@@ -250,9 +311,8 @@ __global__ void k_norm_partial(const C* __restrict__ r, long long n3, double2* _
 
 __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts, double tol_abs,
                              int restart) {
+  const double nn = warp_sum_partials(partial, nparts, 0).x;
   if (threadIdx.x != 0) return;
-  double nn = 0;
-  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
   const double beta = sqrt(nn);
   s->beta = beta;
   s->tol_abs = tol_abs;
@@ -332,9 +392,8 @@ __global__ void k_sub64(const float2* __restrict__ b, const float2* __restrict__
 
 // out[idx] = sqrt(sum partial)
 __global__ void k_norm_final(const double2* __restrict__ partial, int nparts, double* __restrict__ out, int idx) {
+  const double nn = warp_sum_partials(partial, nparts, 0).x;
   if (threadIdx.x != 0) return;
-  double nn = 0;
-  for (int b = 0; b < nparts; ++b) nn += partial[(long long)b * (RMAX + 1)].x;
   out[idx] = sqrt(nn);
 }
 
@@ -477,9 +536,9 @@ static vie_status enqueue_step(vie_plan_s* P) {
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
   for (int pass = 0; pass < 2; ++pass) {
-    { Prof pf_("arnoldi_dot", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part); }
-    { Prof pf_("arnoldi_reduce", st); k_reduce_h<<<1, 128, 0, st>>>(part, s, NPART, pass); }
-    { Prof pf_("arnoldi_update", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1); }
+    { Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part); }
+    { Prof pf_("arnoldi_reduce", st); k_reduce_h<<<1, 1024, 0, st>>>(part, s, NPART, pass); }
+    { Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1); }
     count_launch(3);
   }
   { Prof pf_("givens", st); k_givens<<<1, 32, 0, st>>>(s, part, NPART); }
@@ -494,8 +553,8 @@ static vie_status enqueue_step(vie_plan_s* P) {
 // precision C) is <= tol, or after max_iter steps.  Returns the steps used
 // through *iters and the last true relative residual through *relres.
 template <class C>
-static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol, int max_iter, int* iters,
-                        double* relres) {
+static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol, int max_iter, int max_cycles,
+                        int* iters, double* relres) {
   Krylov& K = *P->kry;
   cudaStream_t st = P->st;
   GmresDev* s = K.state.as<GmresDev>();
@@ -520,8 +579,8 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
   *relres = 0;
   if (bnorm == 0.0) return VIE_OK;
   cudaGraphExec_t& gexec = KB<C>::g(K);
-  int total = 0;
-  double rr = 1.0;
+  int total = 0, cycles = 0;
+  double rr = 1.0, rr_prev = 2.0;
   while (total < max_iter) {
     // cycle start from the current residual rwork
     k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rwork, n3, part);
@@ -576,6 +635,13 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     count_launch(2);
     VIE_TRY(op_Pinv<C>(P, u, z));
     VIE_TRY(axpy_same<C>(x, z, n3, st));
+    if (++cycles >= max_cycles) {
+      // the caller evaluates the residual itself (in higher precision)
+      VIE_CUDA(cudaStreamSynchronize(st));
+      total += hk;
+      rr = -1.0;
+      break;
+    }
     // true residual rwork = rhs - A x
     VIE_TRY(op_A<C>(P, x, w));
     VIE_TRY(sub_same<C>(rhs, w, rwork, n3, st));
@@ -588,6 +654,10 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     total += hk;
     rr = hsc[1] / bnorm;
     if (rr <= tol || hk == 0) break;
+    // restarted cycles that no longer halve the true residual have hit the
+    // rounding floor of this precision
+    if (rr > 0.5 * rr_prev) break;
+    rr_prev = rr;
   }
   *iters = total;
   *relres = rr;
@@ -641,26 +711,31 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
   } else if (!mixed) {
     int it = 0;
     double rr = 0;
-    VIE_TRY(gmres<double2>(P, b, x, r, tol, P->opts.max_iter, &it, &rr));
+    VIE_TRY(gmres<double2>(P, b, x, r, tol, P->opts.max_iter, 1 << 30, &it, &rr));
     inner = it;
     outer = 1;
   } else {
+    // GMRES-IR: each refinement step runs one complex-FP32 GMRES cycle on
+    // A d = r / ||r|| (stopped early once its Arnoldi residual estimate
+    // reaches eta), then x += ||r|| d and r = b - A x in FP64.  Restarts thus
+    // happen in FP64 and the FP32 rounding floor of the inner residual never
+    // limits the outer accuracy.
     VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n3, st));
     VIE_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, st));
     double rn = bnorm;
+    VIE_TRY(norm128(P, r, 3, &rn));   // scal[3] = ||r||, read by the narrowing and the update
+    double rn_prev = 2.0 * bnorm;
+    int stalls = 0;
     while (outer < P->opts.max_refine && inner < P->opts.max_iter) {
       if (rn <= tol * bnorm) break;
-      // rhs64 = r / ||r||  (scal[3] holds ||r||)
-      VIE_TRY(norm128(P, r, 3, &rn));
-      if (rn <= tol * bnorm) break;
+      const double eta = std::max(P->opts.inner_tol, 0.5 * tol * bnorm / rn);
       k_narrow_scaled<<<grid_for(n3), 256, 0, st>>>(r, K.rhs64.as<float2>(), n3, K.scal.as<double>(), 3);
       count_launch();
       int it = 0;
       double rr = 0;
-      VIE_TRY(gmres<float2>(P, K.rhs64.as<float2>(), K.d64.as<float2>(), K.r64.as<float2>(), P->opts.inner_tol,
-                            P->opts.max_iter - inner, &it, &rr));
+      VIE_TRY(gmres<float2>(P, K.rhs64.as<float2>(), K.d64.as<float2>(), K.r64.as<float2>(), eta,
+                            std::min(P->opts.restart, P->opts.max_iter - inner), 1, &it, &rr));
       inner += it;
-      // x += ||r|| d ; r = b - A x (FP64)
       k_axpy_to64<float2><<<grid_for(n3), 256, 0, st>>>(x, K.d64.as<float2>(), n3, K.scal.as<double>(), 3);
       count_launch();
       VIE_TRY(op_A<double2>(P, x, t));
@@ -670,6 +745,10 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
       ++outer;
       VIE_TRY(norm128(P, r, 3, &rn));
       if (it == 0) break;
+      // a step that does not reduce the FP64 residual by 10% (twice in a row)
+      // means the inner solve has nothing left to give
+      if (rn > 0.9 * rn_prev) { if (++stalls >= 2) break; } else stalls = 0;
+      rn_prev = rn;
     }
   }
   // final FP64 residual

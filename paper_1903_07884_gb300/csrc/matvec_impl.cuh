@@ -257,7 +257,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   {                                                                        \
     auto k = k_mv_yz_fwd<C, ME>;                                           \
     VIE_TRY(set_smem(k, smemA));                                           \
-    Prof pf_("mv_yz_fwd", st);                                             \
+    Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);                                             \
     k<<<gA, thA, smemA, st>>>(x, T, d, py, pz, XG);                        \
   }
   VIE_DISPATCH_MAXE(meA, CALL_A)
@@ -280,7 +280,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   {                                                                        \
     auto k = k_mv_x<C, ME>;                                                \
     VIE_TRY(set_smem(k, smemB));                                           \
-    Prof pf_("mv_x", st);                                                  \
+    Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);                                                  \
     k<<<d.Py * d.Pz, thB, smemB, st>>>(T, spec, d, pl, joint);             \
   }
     VIE_DISPATCH_MAXE(meB, CALL_B)
@@ -293,7 +293,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     LineDesc lf = lines_flat(d.nx, d.L, nl, d.nx, 1, d.L, 1);
     if (!S) { set_error("matvec: missing x-spectrum scratch"); return VIE_EINVAL; }
     VIE_TRY(fft_lines<C>(T, S, lf, *P->fL, -1, 1.0, nullptr, st));
-    { Prof pf_("mv_xmul", st); k_mv_xmul<C><<<d.Py * d.Pz, 256, 0, st>>>(S, spec, d); }
+    { Prof pf_(sizeof(C) == 8 ? "mv_xmul_c64" : "mv_xmul_c128", st); k_mv_xmul<C><<<d.Py * d.Pz, 256, 0, st>>>(S, spec, d); }
     count_launch();
     VIE_CHECK_LAUNCH();
     LineDesc li = lines_flat(d.L, d.nx, nl, d.L, 1, d.nx, 1);
@@ -304,7 +304,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   {                                                                        \
     auto k = k_mv_yz_inv<C, ME>;                                           \
     VIE_TRY(set_smem(k, smemA));                                           \
-    Prof pf_("mv_yz_inv", st);                                             \
+    Prof pf_(sizeof(C) == 8 ? "mv_yz_inv_c64" : "mv_yz_inv_c128", st);                                             \
     k<<<gA, thA, smemA, st>>>(T, x, Mv, y, d, py, pz, XG);                 \
   }
   VIE_DISPATCH_MAXE(meA, CALL_C)

@@ -426,13 +426,20 @@ __global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ L
     }
   }
   __syncthreads();
-  // forward substitution with unit lower L
+  // forward substitution with unit lower L: column k of L is staged in
+  // shared memory (one coalesced load per step), then every (row, column)
+  // update reads only shared memory
+  C* col = Y + (size_t)m * CB;   // [m] staged column
   for (int k = 0; k < m - 1; ++k) {
+    for (int i = k + 1 + tid; i < m; i += nt) {
+      const double2 l = LU[(long long)k * m + i];
+      col[i] = cmake<C>((T)l.x, (T)l.y);
+    }
+    __syncthreads();
     const int cnt = (m - k - 1) * cb;
     for (int e = tid; e < cnt; e += nt) {
       const int i = k + 1 + e / cb, c = e % cb;
-      const double2 l = LU[(long long)k * m + i];
-      const C lc = cmake<C>((T)l.x, (T)l.y);
+      const C lc = col[i];
       C y = Y[i * CB + c];
       const C yk = Y[k * CB + c];
       y.x -= lc.x * yk.x - lc.y * yk.y;
@@ -441,20 +448,24 @@ __global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ L
     }
     __syncthreads();
   }
-  // back substitution with U
+  // back substitution with U (column k of U staged likewise)
   for (int k = m - 1; k >= 0; --k) {
-    if (tid < cb) {
-      const double2 u = LU[(long long)k * m + k];
-      const double2 iu = cinv(u);
-      const C ic = cmake<C>((T)iu.x, (T)iu.y);
-      Y[k * CB + tid] = cmul(Y[k * CB + tid], ic);
+    for (int i = tid; i <= k; i += nt) {
+      const double2 u = LU[(long long)k * m + i];
+      if (i == k) {
+        const double2 iu = cinv(u);
+        col[i] = cmake<C>((T)iu.x, (T)iu.y);
+      } else {
+        col[i] = cmake<C>((T)u.x, (T)u.y);
+      }
     }
+    __syncthreads();
+    if (tid < cb) Y[k * CB + tid] = cmul(Y[k * CB + tid], col[k]);
     __syncthreads();
     const int cnt = k * cb;
     for (int e = tid; e < cnt; e += nt) {
       const int i = e / cb, c = e % cb;
-      const double2 u = LU[(long long)k * m + i];
-      const C uc = cmake<C>((T)u.x, (T)u.y);
+      const C uc = col[i];
       C y = Y[i * CB + c];
       const C yk = Y[k * CB + c];
       y.x -= uc.x * yk.x - uc.y * yk.y;
@@ -484,6 +495,8 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
   const int f2 = (n - f) % n;
   const bool pair = (f2 != f);
   const C* D = inv + (long long)s * m * m;
+  const int rows_per = (m + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per, r1 = min(m, r0 + rows_per);
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     r[j] = R[(long long)f * m + j];
     if (pair) {
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < m; i += nw) {
+  for (int i = r0 + warp; i < r1; i += nw) {
     const C* row = D + (long long)i * m;
     C a1 = czero<C>(), a2 = czero<C>();
     for (int j = lane; j < m; j += 32) {
@@ -519,43 +532,60 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
   }
 }
 
-// Discarded frequencies: Z[f] = D_rep^{-1} R[f] for a tile of FT frequencies.
-template <class C, int FT>
-__global__ void __launch_bounds__(256) k_rep_gemm(const C* __restrict__ Drep, const int* __restrict__ disc, int ndisc,
+// Discarded frequencies: Z[f] = D_rep^{-1} R[f], one multi-right-hand-side
+// product.  Register-tiled: a block computes GB_F frequencies x GB_I rows,
+// each thread a 4 x 4 complex micro-tile, with K staged through shared
+// memory GB_K columns at a time.
+constexpr int GB_F = 32, GB_I = 64, GB_K = 16;
+template <class C>
+__global__ void __launch_bounds__(128) k_rep_gemm(const C* __restrict__ Drep, const int* __restrict__ disc, int ndisc,
                                                   const C* __restrict__ R, C* __restrict__ Z, int m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* r = reinterpret_cast<C*>(smem_raw);   // [FT][m]
-  const int t0 = blockIdx.x * FT;
-  const int nt = min(FT, ndisc - t0);
-  for (int e = threadIdx.x; e < FT * m; e += blockDim.x) {
-    const int t = e / m, j = e - t * m;
-    r[e] = t < nt ? R[(long long)disc[t0 + t] * m + j] : czero<C>();
-  }
+  __shared__ C Rs[GB_K][GB_F + 1];
+  __shared__ C Ds[GB_K][GB_I + 1];
+  __shared__ int fidx[GB_F];
+  const int f0 = blockIdx.x * GB_F, i0 = blockIdx.y * GB_I;
+  const int tid = threadIdx.x;
+  const int tf = tid % 8, ti = tid / 8;   // 8 x 16 threads, 4 x 4 outputs each
+  if (tid < GB_F) fidx[tid] = (f0 + tid < ndisc) ? disc[f0 + tid] : -1;
+  C acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = czero<C>();
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = warp; i < m; i += nw) {
-    const C* row = Drep + (long long)i * m;
-    C acc[FT];
-#pragma unroll
-    for (int t = 0; t < FT; ++t) acc[t] = czero<C>();
-    for (int j = lane; j < m; j += 32) {
-      const C d = row[j];
-#pragma unroll
-      for (int t = 0; t < FT; ++t) cfma(acc[t], d, r[t * m + j]);
+  for (int k0 = 0; k0 < m; k0 += GB_K) {
+    for (int e = tid; e < GB_F * GB_K; e += blockDim.x) {
+      const int a = e / GB_K, b = e % GB_K;
+      const int f = fidx[a];
+      Rs[b][a] = (f >= 0 && k0 + b < m) ? R[(long long)f * m + k0 + b] : czero<C>();
     }
-#pragma unroll
-    for (int t = 0; t < FT; ++t) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
-        acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
-      }
+    for (int e = tid; e < GB_I * GB_K; e += blockDim.x) {
+      const int a = e / GB_K, b = e % GB_K;
+      Ds[b][a] = (i0 + a < m && k0 + b < m) ? Drep[(long long)(i0 + a) * m + k0 + b] : czero<C>();
     }
-    if (lane < nt) {
-      C v = acc[0];
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < GB_K; ++k) {
+      C a[4], b[4];
 #pragma unroll
-      for (int t = 1; t < FT; ++t) if (t == lane) v = acc[t];
-      Z[(long long)disc[t0 + lane] * m + i] = v;
+      for (int p = 0; p < 4; ++p) a[p] = Rs[k][tf * 4 + p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = Ds[k][ti * 4 + q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[p][q], b[q], a[p]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int f = fidx[tf * 4 + p];
+    if (f < 0) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + ti * 4 + q;
+      if (i < m) Z[(long long)f * m + i] = acc[p][q];
     }
   }
 }
@@ -672,7 +702,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   dim3 gi(B.nblk, ceil_div(m, CB));
   if (want64) {
     VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
-    const size_t smem = sizeof(float2) * (size_t)m * CB;
+    const size_t smem = sizeof(float2) * (size_t)m * (CB + 1);
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     { Prof pf_("block_inv_c64", st);
       k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB); }
@@ -684,7 +714,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   }
   if (want128) {
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
-    const size_t smem = sizeof(double2) * (size_t)m * CB;
+    const size_t smem = sizeof(double2) * (size_t)m * (CB + 1);
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     { Prof pf_("block_inv_c128", st);
       k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB); }
@@ -765,19 +795,17 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
     // kept blocks (S1 pairs)
     if (B.nhalf > 0) {
       const size_t smem = sizeof(C) * 2 * m;
-      Prof pf_("block_gemv", st);
-      k_block_gemv<C><<<B.nhalf, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, n, nyb * nzb);
+      Prof pf_(sizeof(C) == 8 ? "block_gemv_c64" : "block_gemv_c128", st);
+      dim3 grid(B.nhalf, std::max(1, std::min(8, (4 * 152 + B.nhalf - 1) / B.nhalf)));
+      k_block_gemv<C><<<grid, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, n, nyb * nzb);
       count_launch();
       VIE_CHECK_LAUNCH();
     }
     // discarded frequencies against the representative block
     if (B.ndisc > 0) {
-      constexpr int FT = 8;
-      const size_t smem = sizeof(C) * FT * m;
-      auto kern = k_rep_gemm<C, FT>;
-      if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      Prof pf_("rep_gemm", st);
-      kern<<<ceil_div(B.ndisc, FT), 256, smem, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m);
+      Prof pf_(sizeof(C) == 8 ? "rep_gemm_c64" : "rep_gemm_c128", st);
+      dim3 grid(ceil_div(B.ndisc, GB_F), ceil_div(m, GB_I));
+      k_rep_gemm<C><<<grid, 128, 0, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m);
       count_launch();
       VIE_CHECK_LAUNCH();
     }

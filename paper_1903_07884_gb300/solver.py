@@ -26,7 +26,7 @@ def to_device(a: np.ndarray, device="cuda"):
 
 
 def make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_CIRCULANT, homog=vie.VIE_HOM_REALMEAN,
-              reduce_tol=1e-3, tol=1e-9, restart=50, max_iter=5000, inner_tol=1e-4, max_refine=20,
+              reduce_tol=1e-3, tol=1e-9, restart=50, max_iter=5000, inner_tol=1e-6, max_refine=1000,
               boxes: Optional[Sequence] = None) -> vie.vie_opts:
     return vie.default_opts(precision=precision, precond=precond, homog=homog, reduce_tol=reduce_tol, tol=tol,
                             restart=restart, max_iter=max_iter, inner_tol=inner_tol, max_refine=max_refine,
