@@ -64,6 +64,7 @@ static vie_status upload(const std::vector<std::complex<double>>& v, C** out) {
 
 static vie_status make_plan(int n, FftPlanDev& p64, FftPlanDev& p32) {
   if (!factorize(n, p64)) { set_error("fft: %d is not 7-smooth", n); return VIE_EINVAL; }
+  fft_plan_finalize(p64);
   p32 = p64;
   std::vector<std::complex<double>> tw(n);
   for (int k = 0; k < n; ++k) {
@@ -154,14 +155,14 @@ template <class C> int fft_max_len() { return (int)((200 * 1024) / sizeof(C)) - 
 template int fft_max_len<float2>();
 template int fft_max_len<double2>();
 
-// pre/post modes: 0 none, 1 multiply, 2 multiply by conjugate
+// pre/post modes: 0 none, 1 multiply, 2 multiply by conjugate.
+// MAXE == 0: out-of-place (ping-pong) passes over two tile copies; MAXE > 0:
+// in-place passes, for lines too long to double-buffer.
 template <class C, int MAXE>
-__global__ void __launch_bounds__(1024) k_fft_lines(const C* __restrict__ in, C* __restrict__ out,
-                                                    LineDesc d, FftPlanDev p, int sign, int lpc,
-                                                    const C* __restrict__ pre, int pre_mode,
-                                                    const C* __restrict__ post, int post_mode,
-                                                    const C* __restrict__ post2, int post2_mode,
-                                                    double scale) {
+__global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
+    k_fft_lines(const C* __restrict__ in, C* __restrict__ out, LineDesc d, FftPlanDev p, int sign, int lpc,
+                const C* __restrict__ pre, int pre_mode, const C* __restrict__ post, int post_mode,
+                const C* __restrict__ post2, int post2_mode, double scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   using T = typename real_of<C>::type;
@@ -184,14 +185,19 @@ __global__ void __launch_bounds__(1024) k_fft_lines(const C* __restrict__ in, C*
   }
   __syncthreads();
   SmemLines L{nl, nl, pitch, 0, 1, 0};
-  fft_smem<MAXE>(s, p, L, sign);
+  C* res = s;
+  if constexpr (MAXE == 0) {
+    res = fft_smem_pp(s, s + (size_t)lpc * pitch, p, L, sign);
+  } else {
+    fft_smem<MAXE>(s, p, L, sign);
+  }
   const T sc = (T)scale;
   const int Eo = nl * d.n_out;
   for (int e = threadIdx.x; e < Eo; e += blockDim.x) {
     int li, f;
     if (d.oes == 1) { li = e / d.n_out; f = e - li * d.n_out; } else { f = e / nl; li = e - f * nl; }
     const int l = l0 + li;
-    C v = s[li * pitch + f];
+    C v = res[li * pitch + f];
     if (post_mode) { C w = post[f]; if (post_mode == 2) w.y = -w.y; v = cmul(v, w); }
     if (post2_mode) { C w = post2[f]; if (post2_mode == 2) w.y = -w.y; v = cmul(v, w); }
     const long long off = line_out_off(d, l) + (long long)f * d.oes;
@@ -207,29 +213,38 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
   if (n > fft_max_len<C>()) { set_error("fft: line length %d too long for shared memory", n); return VIE_EINVAL; }
   if (d.nlines <= 0) return VIE_OK;
   const size_t line_bytes = (size_t)(n + 1) * sizeof(C);
-  const size_t budget = 48 * 1024;
+  const bool pp = 2 * line_bytes <= 200 * 1024;
+  const size_t budget = pp ? 24 * 1024 : 48 * 1024;      // per tile copy
   int lpc = (int)(budget / line_bytes);
   if (lpc < 1) lpc = 1;
   if (lpc > d.nlines) lpc = d.nlines;
   if (lpc > 64) lpc = 64;
+  const int grid = (d.nlines + lpc - 1) / lpc;
+  if (pp) {
+    const size_t smem = 2 * (size_t)lpc * line_bytes;
+    auto kern = k_fft_lines<C, 0>;
+    if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);
+    kern<<<grid, 256, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode, post2, post2_mode, scale);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+  }
   const long long E = (long long)lpc * n;
   int threads = 128;
   while (threads < 1024 && E > 8LL * threads) threads *= 2;
   const int per = (int)((E + threads - 1) / threads);
   const size_t smem = (size_t)lpc * line_bytes;
-  const int grid = (d.nlines + lpc - 1) / lpc;
 #define VIE_LAUNCH_LINES(ME)                                                                      \
   {                                                                                               \
     auto kern = k_fft_lines<C, ME>;                                                               \
     if (smem > 48 * 1024)                                                                         \
       VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);                                                                    \
+    Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);                           \
     kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode,  \
                                       post2, post2_mode, scale);                                 \
   }
-  if (per <= 4) VIE_LAUNCH_LINES(4)
-  else if (per <= 8) VIE_LAUNCH_LINES(8)
-  else if (per <= 16) VIE_LAUNCH_LINES(16)
+  if (per <= 16) VIE_LAUNCH_LINES(16)
   else if (per <= 32) VIE_LAUNCH_LINES(32)
   else { set_error("fft: tile of %lld elements too large", E); return VIE_EINVAL; }
 #undef VIE_LAUNCH_LINES

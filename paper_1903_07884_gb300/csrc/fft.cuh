@@ -16,13 +16,45 @@ namespace vie {
 
 constexpr int FFT_MAX_PASSES = 16;
 
+// Exact quotient t / d for 0 <= t, t * d < 2^32 by one high multiply with
+// m = ceil(2^32 / d) (m = 0 encodes d = 1).
+struct FastDiv {
+  unsigned d, m;
+};
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  f.m = d <= 1 ? 0u : (unsigned)((0x100000000ull + d - 1) / d);
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned t, FastDiv f) { return f.m ? __umulhi(t, f.m) : t; }
+
 // Device-side description of one transform length.
 struct FftPlanDev {
   int n;
   int npass;
   int radix[FFT_MAX_PASSES];
   const void* tw;   // n twiddles exp(-2 pi i k / n) in the kernel's complex type
+  // per pass: span Ns before the pass, its fast divisor, butterflies per line
+  // n/R and twiddle stride n/(Ns R)
+  int ns[FFT_MAX_PASSES];
+  FastDiv ns_div[FFT_MAX_PASSES];
+  FastDiv nb_div[FFT_MAX_PASSES];
+  int tws[FFT_MAX_PASSES];
 };
+
+// Fill the per-pass fields from n and the radix list.
+inline void fft_plan_finalize(FftPlanDev& p) {
+  int Ns = 1;
+  for (int i = 0; i < p.npass; ++i) {
+    const int R = p.radix[i];
+    p.ns[i] = Ns;
+    p.ns_div[i] = make_fastdiv((unsigned)Ns);
+    p.nb_div[i] = make_fastdiv((unsigned)(p.n / R));
+    p.tws[i] = p.n / (Ns * R);
+    Ns *= R;
+  }
+}
 
 // Lines in shared memory: line l = l1 + nl1 * l2 (l1 < nl1) starts at
 // l1*ls1 + l2*ls2 and holds element i at offset i*es.
@@ -128,38 +160,54 @@ template <class C> struct Dft<5, C> : DftOdd<5, C> {};
 template <class C> struct Dft<7, C> : DftOdd<7, C> {};
 
 template <class C>
-__device__ __forceinline__ int sl_offset(const SmemLines& L, int line) {
-  const int l1 = line % L.nl1, l2 = line / L.nl1;
+__device__ __forceinline__ int sl_offset(const SmemLines& L, FastDiv nl1, int line) {
+  const int l2 = (int)fdiv((unsigned)line, nl1);
+  const int l1 = line - l2 * L.nl1;
   return l1 * L.ls1 + l2 * L.ls2;
 }
 
 // One radix-R pass over all lines.  MAXE bounds the elements a thread holds:
 // the caller guarantees n * nlines <= MAXE * blockDim.x.
 template <int R, int MAXE, class C>
-__device__ __forceinline__ void fft_pass(C* s, int n, int Ns, const SmemLines& L,
-                                         const C* __restrict__ tw, int sign) {
+__device__ __forceinline__ void fft_pass(C* s, const FftPlanDev& p, int ps, const SmemLines& L, FastDiv nl1,
+                                         FastDiv nlines, const C* __restrict__ tw, int sign) {
   constexpr int MB = (MAXE + R - 1) / R;
+  const int n = p.n;
   const int nb = n / R;
   const int total = nb * L.nlines;
-  const int tws = n / (Ns * R);
+  const int Ns = p.ns[ps];
+  const FastDiv nsd = p.ns_div[ps], nbd = p.nb_div[ps];
+  const int tws = p.tws[ps];
   C v[MB][R];
 #pragma unroll
   for (int b = 0; b < MB; ++b) {
     const int t = threadIdx.x + b * blockDim.x;
     if (t < total) {
       int line, j;
-      if (L.line_fast) { line = t % L.nlines; j = t / L.nlines; }
-      else { line = t / nb; j = t - line * nb; }
-      const C* base = s + sl_offset<C>(L, line);
-      const int k = j % Ns;
+      if (L.line_fast) { j = (int)fdiv((unsigned)t, nlines); line = t - j * L.nlines; }
+      else { line = (int)fdiv((unsigned)t, nbd); j = t - line * nb; }
+      const C* base = s + sl_offset<C>(L, nl1, line);
+      const int k = j - (int)fdiv((unsigned)j, nsd) * Ns;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = base[(j + r * nb) * L.es];
       if (Ns > 1) {
+        if (sizeof(C) == 8) {
+          // FP32: powers of one table twiddle (a few ulp, below the FFT's own error)
+          C w1 = tw[k * tws];
+          if (sign > 0) w1.y = -w1.y;
+          C wr = w1;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w = tw[k * r * tws];
-          if (sign > 0) w.y = -w.y;
-          v[b][r] = cmul(v[b][r], w);
+          for (int r = 1; r < R; ++r) {
+            v[b][r] = cmul(v[b][r], wr);
+            if (r + 1 < R) wr = cmul(wr, w1);
+          }
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            C w = tw[k * r * tws];
+            if (sign > 0) w.y = -w.y;
+            v[b][r] = cmul(v[b][r], w);
+          }
         }
       }
       Dft<R, C>::run(v[b], sign);
@@ -171,11 +219,12 @@ __device__ __forceinline__ void fft_pass(C* s, int n, int Ns, const SmemLines& L
     const int t = threadIdx.x + b * blockDim.x;
     if (t < total) {
       int line, j;
-      if (L.line_fast) { line = t % L.nlines; j = t / L.nlines; }
-      else { line = t / nb; j = t - line * nb; }
-      C* base = s + sl_offset<C>(L, line);
-      const int k = j % Ns;
-      const int o = (j / Ns) * Ns * R + k;
+      if (L.line_fast) { j = (int)fdiv((unsigned)t, nlines); line = t - j * L.nlines; }
+      else { line = (int)fdiv((unsigned)t, nbd); j = t - line * nb; }
+      C* base = s + sl_offset<C>(L, nl1, line);
+      const int jq = (int)fdiv((unsigned)j, nsd);
+      const int k = j - jq * Ns;
+      const int o = jq * Ns * R + k;
 #pragma unroll
       for (int q = 0; q < R; ++q) base[(o + q * Ns) * L.es] = v[b][q];
     }
@@ -185,21 +234,98 @@ __device__ __forceinline__ void fft_pass(C* s, int n, int Ns, const SmemLines& L
 
 // Transform every line in shared memory (sign -1 forward, +1 inverse).
 template <int MAXE, class C>
-__device__ void fft_smem(C* s, const FftPlanDev& p, const SmemLines& L, int sign) {
+__device__ __forceinline__ void fft_smem(C* s, const FftPlanDev& p, const SmemLines& L, int sign) {
   const C* tw = (const C*)p.tw;
-  int Ns = 1;
+  const FastDiv nl1 = make_fastdiv((unsigned)L.nl1);
+  const FastDiv nlines = make_fastdiv((unsigned)L.nlines);
   for (int ps = 0; ps < p.npass; ++ps) {
-    const int R = p.radix[ps];
-    switch (R) {
-      case 8: fft_pass<8, MAXE>(s, p.n, Ns, L, tw, sign); break;
-      case 4: fft_pass<4, MAXE>(s, p.n, Ns, L, tw, sign); break;
-      case 2: fft_pass<2, MAXE>(s, p.n, Ns, L, tw, sign); break;
-      case 3: fft_pass<3, MAXE>(s, p.n, Ns, L, tw, sign); break;
-      case 5: fft_pass<5, MAXE>(s, p.n, Ns, L, tw, sign); break;
-      default: fft_pass<7, MAXE>(s, p.n, Ns, L, tw, sign); break;
+    switch (p.radix[ps]) {
+      case 8: fft_pass<8, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
+      case 4: fft_pass<4, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
+      case 2: fft_pass<2, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
+      case 3: fft_pass<3, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
+      case 5: fft_pass<5, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
+      default: fft_pass<7, MAXE>(s, p, ps, L, nl1, nlines, tw, sign); break;
     }
-    Ns *= R;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Out-of-place (ping-pong) passes: each butterfly reads its R inputs from one
+// shared buffer and writes its R outputs to the other, so a thread holds one
+// butterfly at a time and every pass needs a single barrier.  Used whenever
+// two copies of the tile fit in shared memory.
+// ---------------------------------------------------------------------------
+template <int R, class C>
+__device__ __forceinline__ void fft_pass_pp(const C* __restrict__ in, C* __restrict__ out, const FftPlanDev& p,
+                                            int ps, const SmemLines& L, FastDiv nl1, FastDiv nlines,
+                                            const C* __restrict__ tw, int sign) {
+  const int n = p.n;
+  const int nb = n / R;
+  const int total = nb * L.nlines;
+  const int Ns = p.ns[ps];
+  const FastDiv nsd = p.ns_div[ps], nbd = p.nb_div[ps];
+  const int tws = p.tws[ps];
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int line, j;
+    if (L.line_fast) { j = (int)fdiv((unsigned)t, nlines); line = t - j * L.nlines; }
+    else { line = (int)fdiv((unsigned)t, nbd); j = t - line * nb; }
+    const int off = sl_offset<C>(L, nl1, line);
+    const int jq = (int)fdiv((unsigned)j, nsd);
+    const int k = j - jq * Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[off + (j + r * nb) * L.es];
+    if (Ns > 1) {
+      if (sizeof(C) == 8) {
+        C w1 = tw[k * tws];
+        if (sign > 0) w1.y = -w1.y;
+        C wr = w1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          v[r] = cmul(v[r], wr);
+          if (r + 1 < R) wr = cmul(wr, w1);
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = tw[k * r * tws];
+          if (sign > 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+    }
+    Dft<R, C>::run(v, sign);
+    const int o = jq * Ns * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) out[off + (o + q * Ns) * L.es] = v[q];
+  }
+}
+
+// Transform every line; the data start in buffer a and end in the returned
+// buffer (a or b, same layout).  Ends with a barrier.
+template <class C>
+__device__ __forceinline__ C* fft_smem_pp(C* a, C* b, const FftPlanDev& p, const SmemLines& L, int sign) {
+  const C* tw = (const C*)p.tw;
+  const FastDiv nl1 = make_fastdiv((unsigned)L.nl1);
+  const FastDiv nlines = make_fastdiv((unsigned)L.nlines);
+  C* in = a;
+  C* out = b;
+  for (int ps = 0; ps < p.npass; ++ps) {
+    switch (p.radix[ps]) {
+      case 8: fft_pass_pp<8>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+      case 4: fft_pass_pp<4>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+      case 2: fft_pass_pp<2>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+      case 3: fft_pass_pp<3>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+      case 5: fft_pass_pp<5>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+      default: fft_pass_pp<7>(in, out, p, ps, L, nl1, nlines, tw, sign); break;
+    }
+    __syncthreads();
+    C* t = in;
+    in = out;
+    out = t;
+  }
+  return in;
 }
 
 // ---------------------------------------------------------------------------

@@ -52,7 +52,7 @@ struct BoxPrec {
   DevBuf blkf;               // int [nblk]: frequency of each stored block
   DevBuf inv64;              // float2  [nblk][m][m] row-major D_f^{-1} (mixed path)
   DevBuf inv128;             // double2 [nblk][m][m] row-major D_f^{-1} (FP64 path)
-  DevBuf rhat64, rhat128;    // [n][m] frequency-major work vectors
+  DevBuf rhat64, rhat128;    // [m][n] line-major spectra of the box unknowns
   DevBuf zhat64, zhat128;
   DevBuf tmp64, tmp128;      // Bluestein scratch [m][M] (non-smooth n only)
   const FftLen* fx = nullptr;

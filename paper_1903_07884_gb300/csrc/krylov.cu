@@ -22,7 +22,7 @@
 namespace vie {
 
 constexpr int RMAX = 128;      // largest supported restart length
-constexpr int NPART = 304;     // CTAs of the reduction kernels (2 per SM)
+constexpr int NPART = 608;     // CTAs of the reduction kernels (4 per SM)
 constexpr int RED_THREADS = 256;
 
 struct GmresDev {
@@ -42,7 +42,10 @@ struct GmresDev {
   int done;                       // 1: cycle finished (converged, full, or breakdown)
   int restart;
   int iters;                      // total Arnoldi steps of this state
-  int pad[3];
+  int reorth;                     // 1: second Gram-Schmidt pass needed (DGKS test)
+  int reorths;                    // second passes taken
+  int pad[1];
+  double wnorm0;                  // ||A z|| before orthogonalisation
 };
 
 struct Krylov {
@@ -106,9 +109,9 @@ constexpr int DOT_T = 8;
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
                                                              long long n3, const GmresDev* __restrict__ s,
-                                                             double2* __restrict__ partial) {
+                                                             double2* __restrict__ partial, int pass) {
   __shared__ double2 sh[RED_THREADS / 32][DOT_T];
-  if (s->done) return;
+  if (s->done || (pass == 1 && !s->reorth)) return;
   const int j = s->j;
   const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
   const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
@@ -149,6 +152,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict
     }
     __syncthreads();
   }
+  if (pass == 0) {   // ||w||^2 before orthogonalisation, slot RMAX
+    T nn = 0;
+    for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nn += w[e].x * w[e].x + w[e].y * w[e].y;
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) sh[warp][0] = make_double2((double)nn, 0.0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2][0].x;
+      partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2(t, 0.0);
+    }
+  }
 }
 
 // sum of partial[b][i] over b by one warp (fixed order: lane-strided sums,
@@ -171,9 +186,13 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__
 // hc[i] = sum_b partial[b][i]; mode 0: hsum = hc, mode 1: hsum += hc.
 // One warp per coefficient.
 __global__ void k_reduce_h(const double2* __restrict__ partial, GmresDev* __restrict__ s, int nparts, int mode) {
-  if (s->done) return;
+  if (s->done || (mode == 1 && !s->reorth)) return;
   const int j = s->j;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (mode == 0 && warp == nw - 1) {
+    const double t = warp_sum_partials(partial, nparts, RMAX).x;
+    if (lane == 0) s->wnorm0 = sqrt(t);
+  }
   for (int i = warp; i <= j; i += nw) {
     const double2 t = warp_sum_partials(partial, nparts, i);
     if (lane == 0) {
@@ -188,10 +207,11 @@ __global__ void k_reduce_h(const double2* __restrict__ partial, GmresDev* __rest
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V, C* __restrict__ w, long long n3,
                                                         const GmresDev* __restrict__ s, double2* __restrict__ partial,
-                                                        int want_norm) {
+                                                        int pass) {
   __shared__ double2 sh[32];
   __shared__ C hcs[RMAX + 1];
-  if (s->done) return;
+  if (s->done || (pass == 1 && !s->reorth)) return;
+  const int want_norm = 1;
   const int j = s->j;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) hcs[i] = cconv<C>(s->hc[i]);
   __syncthreads();
@@ -231,6 +251,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V,
       partial[(long long)blockIdx.x * (RMAX + 1)] = make_double2(t, 0.0);
     }
   }
+}
+
+// DGKS test after the first Gram-Schmidt pass: re-orthogonalise only if the
+// projection removed more than 1 - 1/sqrt(2) of ||w||
+__global__ void k_reorth_check(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts) {
+  if (s->done) return;
+  const double nn = warp_sum_partials(partial, nparts, 0).x;
+  if (threadIdx.x != 0) return;
+  const int r = sqrt(nn) < 0.70710678118654752 * s->wnorm0 ? 1 : 0;
+  s->reorth = r;
+  s->reorths += r;
 }
 
 // Hessenberg column, rotations, residual estimate, stop test
@@ -320,6 +351,7 @@ __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict
   s->j = 0;
   s->k = 0;
   s->resest = beta;
+  s->reorth = 0;
   for (int i = 0; i <= restart; ++i) s->g[i] = make_double2(0, 0);
   s->g[0] = make_double2(beta, 0);
   s->done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
@@ -536,10 +568,15 @@ static vie_status enqueue_step(vie_plan_s* P) {
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
   for (int pass = 0; pass < 2; ++pass) {
-    { Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part); }
+    { Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
     { Prof pf_("arnoldi_reduce", st); k_reduce_h<<<1, 1024, 0, st>>>(part, s, NPART, pass); }
-    { Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass == 1); }
+    { Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
     count_launch(3);
+    if (pass == 0) {
+      Prof pf_("reorth_check", st);
+      k_reorth_check<<<1, 32, 0, st>>>(s, part, NPART);
+      count_launch();
+    }
   }
   { Prof pf_("givens", st); k_givens<<<1, 32, 0, st>>>(s, part, NPART); }
   { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s); }

@@ -28,17 +28,18 @@ __device__ __forceinline__ float pair_parity(int c, int axis) {
   return ((A[c] == axis) != (B[c] == axis)) ? -1.f : 1.f;
 }
 
-template <class C, int MAXE>
-__global__ void __launch_bounds__(1024) k_mv_yz_fwd(const C* __restrict__ x, C* __restrict__ T, MvDims d,
-                                                    FftPlanDev py, FftPlanDev pz, int XG) {
+template <class C>
+__global__ void __launch_bounds__(256) k_mv_yz_fwd(const C* __restrict__ x, C* __restrict__ T, MvDims d,
+                                                   FftPlanDev py, FftPlanDev pz, int XG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int b = blockIdx.y;
   const int x0 = blockIdx.x * XG;
   const int xg = min(XG, d.nx - x0);
   const int SP = d.Py * d.Pz + 1;
-  const int total = xg * SP;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) s[e] = czero<C>();
+  C* a = s;
+  C* bb = s + (size_t)XG * SP;
+  for (int e = threadIdx.x; e < 2 * XG * SP; e += blockDim.x) s[e] = czero<C>();
   __syncthreads();
   const long long plane = (long long)d.ny * d.nx;
   const C* xb = x + (long long)b * d.nz * plane;
@@ -47,24 +48,20 @@ __global__ void __launch_bounds__(1024) k_mv_yz_fwd(const C* __restrict__ x, C* 
     const int xl = e % xg;
     const int r = e / xg;
     const int y = r % d.ny, z = r / d.ny;
-    s[xl * SP + z * d.Py + y] = xb[(long long)z * plane + (long long)y * d.nx + x0 + xl];
+    a[xl * SP + z * d.Py + y] = xb[(long long)z * plane + (long long)y * d.nx + x0 + xl];
   }
   __syncthreads();
-  {  // y lines (only the nz non-zero rows)
-    SmemLines L{xg * d.nz, d.nz, d.Py, SP, 1, 0};
-    fft_smem<MAXE>(s, py, L, -1);
-  }
-  {  // z lines (all Py columns)
-    SmemLines L{xg * d.Py, d.Py, 1, SP, d.Py, 1};
-    fft_smem<MAXE>(s, pz, L, -1);
-  }
+  // y lines (only the nz non-zero rows), then z lines (all Py columns); rows
+  // z >= nz stay zero in both buffers
+  C* r1 = fft_smem_pp(a, bb, py, SmemLines{xg * d.nz, d.nz, d.Py, SP, 1, 0}, -1);
+  C* r2 = fft_smem_pp(r1, r1 == a ? bb : a, pz, SmemLines{xg * d.Py, d.Py, 1, SP, d.Py, 1}, -1);
   const int nout = xg * d.Py * d.Pz;
   C* Tb = T + (long long)b * d.Pz * d.Py * d.nx;
   for (int e = threadIdx.x; e < nout; e += blockDim.x) {
     const int xl = e % xg;
     const int r = e / xg;
     const int ky = r % d.Py, kz = r / d.Py;
-    Tb[((long long)kz * d.Py + ky) * d.nx + x0 + xl] = s[xl * SP + kz * d.Py + ky];
+    Tb[((long long)kz * d.Py + ky) * d.nx + x0 + xl] = r2[xl * SP + kz * d.Py + ky];
   }
 }
 
@@ -111,10 +108,12 @@ __device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, i
   }
 }
 
-// fused x pass: shared memory holds the three x-lines of one (ky, kz)
+// fused x pass: shared memory holds the three x-lines of one (ky, kz).
+// MAXE == 0: ping-pong passes over two copies; MAXE > 0: in place (for the
+// longest embeddings).
 template <class C, int MAXE>
-__global__ void __launch_bounds__(1024) k_mv_x(C* __restrict__ T, const C* __restrict__ spec, MvDims d,
-                                               FftPlanDev pl, int joint) {
+__global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024) k_mv_x(C* __restrict__ T, const C* __restrict__ spec,
+                                                                 MvDims d, FftPlanDev pl, int joint) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int kyz = blockIdx.x;
@@ -127,29 +126,29 @@ __global__ void __launch_bounds__(1024) k_mv_x(C* __restrict__ T, const C* __res
     s[e] = i < d.nx ? T[b * lstride + loff + i] : czero<C>();
   }
   __syncthreads();
-  if (joint) {
-    SmemLines Ls{3, 3, L, 0, 1, 0};
-    fft_smem<MAXE>(s, pl, Ls, -1);
+  C* res = s;
+  if constexpr (MAXE == 0) {
+    const SmemLines Ls{3, 3, L, 0, 1, 0};
+    C* r1 = fft_smem_pp(s, s + 3 * L, pl, Ls, -1);
+    tensor_mul(r1, r1 + L, r1 + 2 * L, L, ky, kz, spec, d);
+    __syncthreads();
+    res = fft_smem_pp(r1, r1 == s ? s + 3 * L : s, pl, Ls, +1);
   } else {
-    for (int b = 0; b < 3; ++b) {
-      SmemLines Ls{1, 1, 0, 0, 1, 0};
-      fft_smem<MAXE>(s + b * L, pl, Ls, -1);
-    }
-  }
-  tensor_mul(s, s + L, s + 2 * L, L, ky, kz, spec, d);
-  __syncthreads();
-  if (joint) {
-    SmemLines Ls{3, 3, L, 0, 1, 0};
-    fft_smem<MAXE>(s, pl, Ls, +1);
-  } else {
-    for (int b = 0; b < 3; ++b) {
-      SmemLines Ls{1, 1, 0, 0, 1, 0};
-      fft_smem<MAXE>(s + b * L, pl, Ls, +1);
+    // one call site of the in-place transform keeps register use compact
+    const SmemLines Ls = joint ? SmemLines{3, 3, L, 0, 1, 0} : SmemLines{1, 1, 0, 0, 1, 0};
+    for (int step = 0; step < 2 * (joint ? 1 : 3); ++step) {
+      const int dir = joint ? step : step / 3;
+      const int b = joint ? 0 : step % 3;
+      fft_smem<MAXE>(s + b * L, pl, Ls, dir == 0 ? -1 : +1);
+      if (step == (joint ? 0 : 2)) {
+        tensor_mul(s, s + L, s + 2 * L, L, ky, kz, spec, d);
+        __syncthreads();
+      }
     }
   }
   for (int e = threadIdx.x; e < 3 * d.nx; e += blockDim.x) {
     const int a = e / d.nx, i = e - a * d.nx;
-    T[a * lstride + loff + i] = s[a * L + i];
+    T[a * lstride + loff + i] = res[a * L + i];
   }
 }
 
@@ -165,33 +164,30 @@ __global__ void k_mv_xmul(C* __restrict__ S, const C* __restrict__ spec, MvDims 
   tensor_mul(s0, s0 + lstride, s0 + 2 * lstride, d.L, ky, kz, spec, d);
 }
 
-template <class C, int MAXE>
-__global__ void __launch_bounds__(1024) k_mv_yz_inv(const C* __restrict__ T, const C* __restrict__ x,
-                                                    const C* __restrict__ Mv, C* __restrict__ y, MvDims d,
-                                                    FftPlanDev py, FftPlanDev pz, int XG) {
+template <class C>
+__global__ void __launch_bounds__(256) k_mv_yz_inv(const C* __restrict__ T, const C* __restrict__ x,
+                                                   const C* __restrict__ Mv, C* __restrict__ y, MvDims d,
+                                                   FftPlanDev py, FftPlanDev pz, int XG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int a = blockIdx.y;
   const int x0 = blockIdx.x * XG;
   const int xg = min(XG, d.nx - x0);
   const int SP = d.Py * d.Pz + 1;
+  C* ba = s;
+  C* bb = s + (size_t)XG * SP;
   const C* Ta = T + (long long)a * d.Pz * d.Py * d.nx;
   const int nin = xg * d.Py * d.Pz;
   for (int e = threadIdx.x; e < nin; e += blockDim.x) {
     const int xl = e % xg;
     const int r = e / xg;
     const int ky = r % d.Py, kz = r / d.Py;
-    s[xl * SP + kz * d.Py + ky] = Ta[((long long)kz * d.Py + ky) * d.nx + x0 + xl];
+    ba[xl * SP + kz * d.Py + ky] = Ta[((long long)kz * d.Py + ky) * d.nx + x0 + xl];
   }
   __syncthreads();
-  {  // z lines (all Py columns)
-    SmemLines L{xg * d.Py, d.Py, 1, SP, d.Py, 1};
-    fft_smem<MAXE>(s, pz, L, +1);
-  }
-  {  // y lines (only the nz rows kept)
-    SmemLines L{xg * d.nz, d.nz, d.Py, SP, 1, 0};
-    fft_smem<MAXE>(s, py, L, +1);
-  }
+  // z lines (all Py columns), then y lines (only the nz rows kept)
+  C* r1 = fft_smem_pp(ba, bb, pz, SmemLines{xg * d.Py, d.Py, 1, SP, d.Py, 1}, +1);
+  C* r2 = fft_smem_pp(r1, r1 == ba ? bb : ba, py, SmemLines{xg * d.nz, d.nz, d.Py, SP, 1, 0}, +1);
   const long long plane = (long long)d.ny * d.nx;
   const long long off_a = (long long)a * d.nz * plane;
   const int nout = xg * d.ny * d.nz;
@@ -202,7 +198,7 @@ __global__ void __launch_bounds__(1024) k_mv_yz_inv(const C* __restrict__ T, con
     const long long v = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
     const C xv = x[off_a + v];
     const C m = Mv[v];
-    const C g = s[xl * SP + z * d.Py + yy];
+    const C g = r2[xl * SP + z * d.Py + yy];
     // y = x - M (x + Gx)
     const C t = cadd(xv, g);
     y[off_a + v] = csub(xv, cmul(m, t));
@@ -212,7 +208,9 @@ __global__ void __launch_bounds__(1024) k_mv_yz_inv(const C* __restrict__ T, con
 static inline int pick_xg(const MvDims& d, size_t csize) {
   const size_t slab = (size_t)(d.Py * d.Pz + 1) * csize;
   int xg = 32;
-  while (xg > 2 && (size_t)xg * slab > 96 * 1024) xg /= 2;
+  // two tile copies within about 64 KB: several blocks per SM and at least
+  // two blocks per SM over the grid for the usual sizes
+  while (xg > 1 && 2 * (size_t)xg * slab > 64 * 1024) xg /= 2;
   if (xg > d.nx) xg = std::max(1, d.nx);
   return xg;
 }
@@ -248,43 +246,45 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   const int cap = 16;
   // pass A
   const int XG = pick_xg(d, sizeof(C));
-  const size_t smemA = (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
-  int meA;
-  const int thA = threads_for((long long)XG * d.Py * d.Pz, meA, cap);
+  const size_t smemA = 2 * (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
   dim3 gA(ceil_div(d.nx, XG), 3);
   const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
-#define CALL_A(ME)                                                         \
-  {                                                                        \
-    auto k = k_mv_yz_fwd<C, ME>;                                           \
-    VIE_TRY(set_smem(k, smemA));                                           \
-    Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);                                             \
-    k<<<gA, thA, smemA, st>>>(x, T, d, py, pz, XG);                        \
+  {
+    auto k = k_mv_yz_fwd<C>;
+    VIE_TRY(set_smem(k, smemA));
+    Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);
+    k<<<gA, 256, smemA, st>>>(x, T, d, py, pz, XG);
   }
-  VIE_DISPATCH_MAXE(meA, CALL_A)
-#undef CALL_A
   count_launch();
   VIE_CHECK_LAUNCH();
   // pass B
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
   if (fused) {
-    const size_t smemB = (size_t)3 * d.L * sizeof(C);
-    int meB;
-    int joint = 1;
-    int thB = threads_for(3LL * d.L, meB, cap);
-    if ((long long)meB * thB < 3LL * d.L || meB > cap) {
-      joint = 0;
-      thB = threads_for((long long)d.L, meB, cap);
-    }
-    if ((long long)meB * thB < (joint ? 3LL : 1LL) * d.L) { set_error("matvec: x line too long"); return VIE_EINVAL; }
+    const size_t tile = (size_t)3 * d.L * sizeof(C);
+    if (2 * tile <= 200 * 1024) {
+      auto k = k_mv_x<C, 0>;
+      VIE_TRY(set_smem(k, 2 * tile));
+      Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);
+      k<<<d.Py * d.Pz, 256, 2 * tile, st>>>(T, spec, d, pl, 1);
+    } else {
+      int meB;
+      int joint = 1;
+      int thB = threads_for(3LL * d.L, meB, cap);
+      if ((long long)meB * thB < 3LL * d.L || meB > cap) {
+        joint = 0;
+        thB = threads_for((long long)d.L, meB, cap);
+      }
+      if ((long long)meB * thB < (joint ? 3LL : 1LL) * d.L) { set_error("matvec: x line too long"); return VIE_EINVAL; }
 #define CALL_B(ME)                                                         \
   {                                                                        \
     auto k = k_mv_x<C, ME>;                                                \
-    VIE_TRY(set_smem(k, smemB));                                           \
-    Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);                                                  \
-    k<<<d.Py * d.Pz, thB, smemB, st>>>(T, spec, d, pl, joint);             \
+    VIE_TRY(set_smem(k, tile));                                            \
+    Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);               \
+    k<<<d.Py * d.Pz, thB, tile, st>>>(T, spec, d, pl, joint);              \
   }
-    VIE_DISPATCH_MAXE(meB, CALL_B)
+      VIE_DISPATCH_MAXE(meB, CALL_B)
 #undef CALL_B
+    }
     count_launch();
     VIE_CHECK_LAUNCH();
   } else {
@@ -300,19 +300,15 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, nullptr, st));
   }
   // pass C
-#define CALL_C(ME)                                                         \
-  {                                                                        \
-    auto k = k_mv_yz_inv<C, ME>;                                           \
-    VIE_TRY(set_smem(k, smemA));                                           \
-    Prof pf_(sizeof(C) == 8 ? "mv_yz_inv_c64" : "mv_yz_inv_c128", st);                                             \
-    k<<<gA, thA, smemA, st>>>(T, x, Mv, y, d, py, pz, XG);                 \
+  {
+    auto k = k_mv_yz_inv<C>;
+    VIE_TRY(set_smem(k, smemA));
+    Prof pf_(sizeof(C) == 8 ? "mv_yz_inv_c64" : "mv_yz_inv_c128", st);
+    k<<<gA, 256, smemA, st>>>(T, x, Mv, y, d, py, pz, XG);
   }
-  VIE_DISPATCH_MAXE(meA, CALL_C)
-#undef CALL_C
   count_launch();
   VIE_CHECK_LAUNCH();
   return VIE_OK;
 }
-
 
 }  // namespace vie

@@ -9,7 +9,7 @@
 // the matvec intermediate), so this entry point takes only the caller's
 // buffers and keeps every temporary -- FFT twiddles, the material operator,
 // the generator spectra and the yz-transformed intermediate -- in one
-// file-scope device array of VIE_STATIC_SCRATCH_BYTES.  That array is part of
+// file-scope device array of kStaticScratchBytes (64 MiB).  That array is part of
 // the library image: every GPU that loads libvie holds it until the process
 // exits, used or not.
 //
@@ -83,7 +83,9 @@ static bool factor_radices(int n, FftPlanDev& p) {
       p.radix[p.npass++] = r;
       m /= r;
     }
-  return m == 1;
+  if (m != 1) return false;
+  fft_plan_finalize(p);
+  return true;
 }
 
 struct Carve {

@@ -498,9 +498,9 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
   const int rows_per = (m + gridDim.y - 1) / gridDim.y;
   const int r0 = blockIdx.y * rows_per, r1 = min(m, r0 + rows_per);
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    r[j] = R[(long long)f * m + j];
+    r[j] = R[(long long)j * n + f];
     if (pair) {
-      C v = R[(long long)f2 * m + j];
+      C v = R[(long long)j * n + f2];
       if (j < ny_nz) { v.x = -v.x; v.y = -v.y; }
       r[m + j] = v;
     }
@@ -523,69 +523,83 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
       a2.y += __shfl_xor_sync(0xffffffffu, a2.y, o);
     }
     if (lane == 0) {
-      Z[(long long)f * m + i] = a1;
+      Z[(long long)i * n + f] = a1;
       if (pair) {
         if (i < ny_nz) { a2.x = -a2.x; a2.y = -a2.y; }
-        Z[(long long)f2 * m + i] = a2;
+        Z[(long long)i * n + f2] = a2;
       }
     }
   }
 }
 
 // Discarded frequencies: Z[f] = D_rep^{-1} R[f], one multi-right-hand-side
-// product.  Register-tiled: a block computes GB_F frequencies x GB_I rows,
-// each thread a 4 x 4 complex micro-tile, with K staged through shared
-// memory GB_K columns at a time.
+// product.  Register-tiled: a block of 256 threads computes GB_F frequencies
+// x GB_I rows, each thread a 2 x 4 complex micro-tile; K advances GB_K
+// columns at a time through shared memory, the next tile prefetched into
+// registers while the current one is consumed.
 constexpr int GB_F = 32, GB_I = 64, GB_K = 16;
 template <class C>
-__global__ void __launch_bounds__(128) k_rep_gemm(const C* __restrict__ Drep, const int* __restrict__ disc, int ndisc,
-                                                  const C* __restrict__ R, C* __restrict__ Z, int m) {
-  __shared__ C Rs[GB_K][GB_F + 1];
-  __shared__ C Ds[GB_K][GB_I + 1];
+__global__ void __launch_bounds__(256) k_rep_gemm(const C* __restrict__ Drep, const int* __restrict__ disc, int ndisc,
+                                                  const C* __restrict__ R, C* __restrict__ Z, int m, int n) {
+  __shared__ C Rs[GB_K][GB_F];
+  __shared__ C Ds[GB_K][GB_I];
   __shared__ int fidx[GB_F];
   const int f0 = blockIdx.x * GB_F, i0 = blockIdx.y * GB_I;
   const int tid = threadIdx.x;
-  const int tf = tid % 8, ti = tid / 8;   // 8 x 16 threads, 4 x 4 outputs each
+  const int tf = tid % 16, ti = tid / 16;   // 16 x 16 threads: 2 frequencies x 4 rows each
   if (tid < GB_F) fidx[tid] = (f0 + tid < ndisc) ? disc[f0 + tid] : -1;
-  C acc[4][4];
+  __syncthreads();
+  // global -> register staging: R tile 32x16 (2 per thread), D tile 64x16 (4 per thread)
+  C rr[2], dr[4];
+  auto fetch = [&](int k0) {
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+    for (int u = 0; u < 2; ++u) {
+      // consecutive threads walk consecutive frequencies of one row p
+      const int e = tid + u * 256, a = e % GB_F, b = e / GB_F;
+      const int f = fidx[a];
+      rr[u] = (f >= 0 && k0 + b < m) ? R[(long long)(k0 + b) * n + f] : czero<C>();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256, a = e / GB_K, b = e % GB_K;
+      dr[u] = (i0 + a < m && k0 + b < m) ? Drep[(long long)(i0 + a) * m + k0 + b] : czero<C>();
+    }
+  };
+  C acc[2][4];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[p][q] = czero<C>();
-  __syncthreads();
+  fetch(0);
   for (int k0 = 0; k0 < m; k0 += GB_K) {
-    for (int e = tid; e < GB_F * GB_K; e += blockDim.x) {
-      const int a = e / GB_K, b = e % GB_K;
-      const int f = fidx[a];
-      Rs[b][a] = (f >= 0 && k0 + b < m) ? R[(long long)f * m + k0 + b] : czero<C>();
-    }
-    for (int e = tid; e < GB_I * GB_K; e += blockDim.x) {
-      const int a = e / GB_K, b = e % GB_K;
-      Ds[b][a] = (i0 + a < m && k0 + b < m) ? Drep[(long long)(i0 + a) * m + k0 + b] : czero<C>();
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < GB_K; ++k) {
-      C a[4], b[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) a[p] = Rs[k][tf * 4 + p];
+    for (int u = 0; u < 2; ++u) { const int e = tid + u * 256; Rs[e / GB_F][e % GB_F] = rr[u]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { const int e = tid + u * 256; Ds[e % GB_K][e / GB_K] = dr[u]; }
+    __syncthreads();
+    if (k0 + GB_K < m) fetch(k0 + GB_K);
+#pragma unroll
+    for (int k = 0; k < GB_K; ++k) {
+      C a[2], b[4];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) a[p] = Rs[k][tf * 2 + p];
 #pragma unroll
       for (int q = 0; q < 4; ++q) b[q] = Ds[k][ti * 4 + q];
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 2; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) cfma(acc[p][q], b[q], a[p]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int f = fidx[tf * 4 + p];
+  for (int p = 0; p < 2; ++p) {
+    const int f = fidx[tf * 2 + p];
     if (f < 0) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = i0 + ti * 4 + q;
-      if (i < m) Z[(long long)f * m + i] = acc[p][q];
+      if (i < m) Z[(long long)i * n + f] = acc[p][q];
     }
   }
 }
@@ -786,10 +800,10 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
     const int n = B.n, m = B.m, nyb = B.b.ny, nzb = B.b.nz;
     C* rh = BoxBufs<C>::rh(B);
     C* zh = BoxBufs<C>::zh(B);
-    // gather + x-FFT: line p = (alpha, zb, yb) -> R[f][p]
+    // gather + x-FFT: line p = (alpha, zb, yb) -> R[p][f] (line-major)
     LineDesc ld{n, n, m, nyb, nzb,
                 (long long)P->nx, (long long)P->ny * P->nx, N, 1,
-                1, (long long)nyb, (long long)nyb * nzb, (long long)m};
+                (long long)n, (long long)nyb * n, (long long)nyb * nzb * n, 1};
     const long long base = ((long long)B.b.z0 * P->ny + B.b.y0) * P->nx + B.b.x0;
     VIE_TRY(fft_lines<C>(r + base, rh, ld, *B.fx, -1, 1.0, BoxBufs<C>::tmp(B), st));
     // kept blocks (S1 pairs)
@@ -805,13 +819,13 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
     if (B.ndisc > 0) {
       Prof pf_(sizeof(C) == 8 ? "rep_gemm_c64" : "rep_gemm_c128", st);
       dim3 grid(ceil_div(B.ndisc, GB_F), ceil_div(m, GB_I));
-      k_rep_gemm<C><<<grid, 128, 0, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m);
+      k_rep_gemm<C><<<grid, 256, 0, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m, n);
       count_launch();
       VIE_CHECK_LAUNCH();
     }
     // inverse x-FFT + scatter
     LineDesc lo{n, n, m, nyb, nzb,
-                1, (long long)nyb, (long long)nyb * nzb, (long long)m,
+                (long long)n, (long long)nyb * n, (long long)nyb * nzb * n, 1,
                 (long long)P->nx, (long long)P->ny * P->nx, N, 1};
     VIE_TRY(fft_lines<C>(zh, z + base, lo, *B.fx, +1, 1.0 / n, BoxBufs<C>::tmp(B), st));
   }
