@@ -235,23 +235,31 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   d.L = embed_len(nx); d.Py = embed_len(ny); d.Pz = embed_len(nz);
   d.Lh = d.L / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
   if ((long long)d.Py * d.Pz > 4096) { set_error("vie_plan_create: cross-section too large (Py*Pz > 4096)"); return VIE_EINVAL; }
-  if (d.L > fft_max_len<double2>()) {
-    set_error("vie_plan_create: nx=%d needs an x-embedding of %d > %d points", nx, d.L, fft_max_len<double2>());
+  if (d.L > 2 * fft_max_len<double2>()) {
+    set_error("vie_plan_create: nx=%d needs an x-embedding of %d > %d points", nx, d.L, 2 * fft_max_len<double2>());
     return VIE_EINVAL;
   }
   for (const vie_box& b : P->boxes) {
     const FftLen* f;
     VIE_TRY(fft_get(b.nx, &f));
-    const int lim = o.precision == VIE_FP64 ? fft_max_len<double2>() : fft_max_len<float2>();
+    // the Chan eigenvalues are transformed in FP64; one split doubles the limit
     const int len = f->bluestein ? f->M : f->n;
-    if (len > lim || (f->bluestein && len > fft_max_len<double2>())) {
+    if (len > 2 * fft_max_len<double2>()) {
       set_error("vie_plan_create: box length %d needs a transform of %d points (limit %d)", b.nx, len,
-                fft_max_len<double2>());
+                2 * fft_max_len<double2>());
       return VIE_EINVAL;
+    }
+    if (len > fft_max_len<double2>()) {
+      const FftLen* h;
+      VIE_TRY(fft_get(len / 2, &h));   // half length used by the split, cached before any capture
     }
     if (3 * b.ny * b.nz > 1152) { set_error("vie_plan_create: box cross-section too large (m > 1152)"); return VIE_EINVAL; }
   }
   VIE_TRY(fft_get(d.L, &P->fL));
+  if (d.L > fft_max_len<float2>() || d.L > fft_max_len<double2>()) {
+    const FftLen* h;
+    VIE_TRY(fft_get(d.L / 2, &h));   // half length used by the split, cached before any capture
+  }
   VIE_TRY(fft_get(d.Py, &P->fPy));
   VIE_TRY(fft_get(d.Pz, &P->fPz));
   VIE_TRY(build_spectra(P.get()));
@@ -375,6 +383,7 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
   const double full = L * Py * Pz * 16;                  // spectra assembly scratch
   const double T = 3.0 * Pz * Py * nx * (16 + 8);
   const double Sx = (3.0 * L * 16 > 200 * 1024) ? 3.0 * Pz * Py * L * (16 + 8) : 0;
+  const double Xs = (L > 12736) ? 3.0 * Pz * Py * L * 16 + L * Py * Pz * 16 : 0;   // long-line split scratch
   const double vec = N * 3 * (16 * 6 + 8 * 8) + N * 24;
   const int R = o.restart;
   const double basis = N * 3 * (R + 1) * (o.precision == VIE_MIXED ? 8 : 16);
@@ -392,7 +401,7 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
       prec += lam + blocks + 4.0 * b.nx * m * 16;
     }
   }
-  return (size_t)(spec + full + T + Sx + vec + basis + prec + 64.0 * 1024 * 1024);
+  return (size_t)(spec + full + T + Sx + Xs + vec + basis + prec + 64.0 * 1024 * 1024);
 }
 
 }  // extern "C"

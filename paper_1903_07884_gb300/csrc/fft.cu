@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 
+#include <algorithm>
 #include <atomic>
 #include <complex>
 #include <map>
@@ -161,8 +162,8 @@ template int fft_max_len<double2>();
 template <class C, int MAXE>
 __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
     k_fft_lines(const C* __restrict__ in, C* __restrict__ out, LineDesc d, FftPlanDev p, int sign, int lpc,
-                const C* __restrict__ pre, int pre_mode, const C* __restrict__ post, int post_mode,
-                const C* __restrict__ post2, int post2_mode, double scale) {
+                const C* __restrict__ pre, int pre_mode, int pre_stride, int pre_off, const C* __restrict__ post,
+                int post_mode, const C* __restrict__ post2, int post2_mode, double scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   using T = typename real_of<C>::type;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
     if (i < d.n_in) {
       const long long off = line_in_off(d, l) + (long long)i * d.ies;
       v = in[off];
-      if (pre_mode) { C w = pre[i]; if (pre_mode == 2) w.y = -w.y; v = cmul(v, w); }
+      if (pre_mode) { C w = pre[i * pre_stride + pre_off]; if (pre_mode == 2) w.y = -w.y; v = cmul(v, w); }
     }
     s[li * pitch + i] = v;
   }
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
 
 template <class C>
 static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const FftPlanDev& p, int sign,
-                               const C* pre, int pre_mode, const C* post, int post_mode,
+                               const C* pre, int pre_mode, int pre_stride, int pre_off, const C* post, int post_mode,
                                const C* post2, int post2_mode, double scale, cudaStream_t st) {
   const int n = p.n;
   if (n > fft_max_len<C>()) { set_error("fft: line length %d too long for shared memory", n); return VIE_EINVAL; }
@@ -225,7 +226,8 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
     auto kern = k_fft_lines<C, 0>;
     if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);
-    kern<<<grid, 256, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode, post2, post2_mode, scale);
+    kern<<<grid, 256, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, pre_stride, pre_off, post, post_mode,
+                                  post2, post2_mode, scale);
     count_launch();
     VIE_CHECK_LAUNCH();
     return VIE_OK;
@@ -241,8 +243,8 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
     if (smem > 48 * 1024)                                                                         \
       VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);                           \
-    kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, post, post_mode,  \
-                                      post2, post2_mode, scale);                                 \
+    kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, pre_stride, pre_off, \
+                                      post, post_mode, post2, post2_mode, scale);                \
   }
   if (per <= 16) VIE_LAUNCH_LINES(16)
   else if (per <= 32) VIE_LAUNCH_LINES(32)
@@ -265,27 +267,94 @@ template <> struct Tabs<float2> {
   static const float2* hati(const FftLen& f) { return f.hati32; }
 };
 
+// y[j] = post[j] * scale * (E[j mod n/2] + w^j O[j mod n/2]), w = exp(sign 2 pi i / n):
+// the decimation-in-time combination of the two half-length transforms of
+// the even- and odd-indexed inputs.
 template <class C>
-vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, int sign, double scale,
-                     C* tmp, cudaStream_t st) {
+__global__ void k_dit_combine(const C* __restrict__ E, const C* __restrict__ O, C* __restrict__ out, LineDesc d,
+                              int n, const C* __restrict__ tw, int sign, const C* __restrict__ post, int post_mode,
+                              double scale) {
+  using T = typename real_of<C>::type;
+  const int n2 = n / 2;
+  const long long total = (long long)d.nlines * d.n_out;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / d.n_out), j = (int)(idx - (long long)l * d.n_out);
+    const int jh = j < n2 ? j : j - n2;
+    C w = tw[j];
+    if (sign > 0) w.y = -w.y;
+    C v = cadd(E[(long long)l * n2 + jh], cmul(w, O[(long long)l * n2 + jh]));
+    if (post_mode) { C q = post[j]; if (post_mode == 2) q.y = -q.y; v = cmul(v, q); }
+    out[line_out_off(d, l) + (long long)j * d.oes] = cscale(v, (T)scale);
+  }
+}
+
+// Transform of length p.n with optional multipliers; lines longer than
+// shared memory holds are split once by decimation in time (scratch: nlines
+// * p.n elements).
+template <class C>
+static vie_status launch_len(const C* in, C* out, const LineDesc& d, const FftPlanDev& p, int sign, const C* pre,
+                             int pre_mode, const C* post, int post_mode, double scale, C* split_tmp, cudaStream_t st) {
+  if (p.n <= fft_max_len<C>())
+    return launch_lines<C>(in, out, d, p, sign, pre, pre_mode, 1, 0, post, post_mode, nullptr, 0, scale, st);
+  const int n = p.n, n2 = n / 2;
+  if (n % 2 || n2 > fft_max_len<C>()) { set_error("fft: length %d too long", n); return VIE_EINVAL; }
+  if (!split_tmp) { set_error("fft: length %d needs split scratch", n); return VIE_EINVAL; }
+  const FftLen* h;
+  VIE_TRY(fft_get(n2, &h));
+  const FftPlanDev& ph = plan_n<C>(*h);
+  C* E = split_tmp;
+  C* O = split_tmp + (size_t)d.nlines * n2;
+  // half transforms of the even / odd inputs (their multipliers at indices 2j, 2j + 1)
+  LineDesc de = d;
+  de.ies = 2 * d.ies;
+  de.n_in = (d.n_in + 1) / 2;
+  de.n_out = n2;
+  de.os1 = n2; de.os2 = (long long)n2 * d.nl1; de.os3 = (long long)n2 * d.nl1 * d.nl2; de.oes = 1;
+  VIE_TRY(launch_lines<C>(in, E, de, ph, sign, pre, pre_mode, 2, 0, nullptr, 0, nullptr, 0, 1.0, st));
+  LineDesc dod = de;
+  dod.n_in = d.n_in / 2;
+  VIE_TRY(launch_lines<C>(in + d.ies, O, dod, ph, sign, pre, pre_mode, 2, 1, nullptr, 0, nullptr, 0, 1.0, st));
+  const long long total = (long long)d.nlines * d.n_out;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_dit_combine<C><<<grid, 256, 0, st>>>(E, O, out, d, n, (const C*)p.tw, sign, post, post_mode, scale);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+template <class C>
+size_t fft_scratch_elems(const FftLen& f, int nlines) {
+  const size_t len = f.bluestein ? (size_t)f.M : (size_t)f.n;
+  size_t s = 0;
+  if (f.bluestein) s += (size_t)nlines * len;
+  if (len > (size_t)fft_max_len<C>()) s += (size_t)nlines * len;
+  return s;
+}
+template size_t fft_scratch_elems<float2>(const FftLen&, int);
+template size_t fft_scratch_elems<double2>(const FftLen&, int);
+
+template <class C>
+vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, int sign, double scale, C* tmp,
+                     cudaStream_t st) {
   if (d.n_in > f.n || d.n_out > f.n) { set_error("fft: line desc exceeds length"); return VIE_EINVAL; }
   if (!f.bluestein) {
-    return launch_lines<C>(in, out, d, plan_n<C>(f), sign, nullptr, 0, nullptr, 0, nullptr, 0, scale, st);
+    return launch_len<C>(in, out, d, plan_n<C>(f), sign, nullptr, 0, nullptr, 0, scale, tmp, st);
   }
   if (!tmp) { set_error("fft: Bluestein length %d needs a scratch buffer", f.n); return VIE_EINVAL; }
+  C* split = f.M > fft_max_len<C>() ? tmp + (size_t)d.nlines * f.M : nullptr;
   // step 1: a_k = x_k * conj(b_k) (forward) or x_k * b_k (inverse), FFT_M, times chirp spectrum
   LineDesc d1 = d;
   d1.os1 = f.M; d1.os2 = (long long)f.M * d.nl1; d1.os3 = (long long)f.M * d.nl1 * d.nl2;
   d1.oes = 1; d1.n_out = f.M;
   const C* chirp = Tabs<C>::chirp(f);
   const C* hat = sign < 0 ? Tabs<C>::hatf(f) : Tabs<C>::hati(f);
-  VIE_TRY(launch_lines<C>(in, tmp, d1, plan_n<C>(f), -1, chirp, sign < 0 ? 2 : 1, hat, 1, nullptr, 0, 1.0, st));
+  VIE_TRY(launch_len<C>(in, tmp, d1, plan_n<C>(f), -1, chirp, sign < 0 ? 2 : 1, hat, 1, 1.0, split, st));
   // step 2: inverse FFT_M (the 1/M is in the chirp spectrum), times conj(b_f) or b_f
   LineDesc d2 = d;
   d2.n_in = f.M; d2.is1 = f.M; d2.is2 = (long long)f.M * d.nl1; d2.is3 = (long long)f.M * d.nl1 * d.nl2;
   d2.ies = 1;
-  return launch_lines<C>(tmp, out, d2, plan_n<C>(f), +1, nullptr, 0, chirp, sign < 0 ? 2 : 1,
-                         nullptr, 0, scale, st);
+  return launch_len<C>(tmp, out, d2, plan_n<C>(f), +1, nullptr, 0, chirp, sign < 0 ? 2 : 1, scale, split, st);
 }
 
 template vie_status fft_lines<double2>(const double2*, double2*, const LineDesc&, const FftLen&, int,

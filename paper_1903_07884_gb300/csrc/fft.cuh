@@ -386,16 +386,22 @@ inline LineDesc lines_flat(int n_in, int n_out, int nlines, long long is, long l
 }
 
 // Batched FFT of lines through shared memory, any supported length (smooth
-// lengths directly; others by Bluestein through `tmp`, which must hold
-// nlines * M elements of the working type).  sign -1 forward, +1 inverse
+// lengths directly; others by Bluestein; lines longer than shared memory by
+// one decimation-in-time split).  `tmp` must hold fft_scratch_elems<C>(f,
+// nlines) elements when that is non-zero.  sign -1 forward, +1 inverse
 // (unnormalised); `scale` multiplies every output.  Out-of-place or in place
 // when input and output footprints coincide.
 template <class C>
 vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, int sign,
                      double scale, C* tmp, cudaStream_t st);
 
-// Largest line length that fft_lines can hold in shared memory for type C.
+// Largest line length that fft_lines can hold in shared memory for type C
+// (longer even lengths, up to twice this, are split once).
 template <class C> int fft_max_len();
+
+// Scratch elements (of type C) that fft_lines needs for nlines lines of this
+// transform length: Bluestein buffer and/or the split of an over-long line.
+template <class C> size_t fft_scratch_elems(const FftLen& f, int nlines);
 
 void count_launch(int n = 1);
 

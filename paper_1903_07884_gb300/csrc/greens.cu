@@ -64,8 +64,10 @@ vie_status build_spectra(vie_plan_s* P) {
   const long long Q = (long long)d.Lh * d.Pyh * d.Pzh;
   VIE_TRY(P->spec128.alloc(sizeof(double2) * 6 * Q));
   VIE_TRY(P->spec64.alloc(sizeof(float2) * 6 * Q));
-  DevBuf full;
+  DevBuf full, xsplit;
   VIE_TRY(full.alloc(sizeof(double2) * Pn));
+  const size_t xs = fft_scratch_elems<double2>(*P->fL, d.Py * d.Pz);
+  if (xs) VIE_TRY(xsplit.alloc(sizeof(double2) * xs));
   const double2 self = self_term_value(P->h, P->kb);
   const int threads = 256;
   const int grid = (int)std::min<long long>((Pn + threads - 1) / threads, 152LL * 16);
@@ -76,7 +78,7 @@ vie_status build_spectra(vie_plan_s* P) {
     double2* f = full.as<double2>();
     // x lines: contiguous, Py*Pz of them
     LineDesc lx = lines_flat(d.L, d.L, d.Py * d.Pz, d.L, 1, d.L, 1);
-    VIE_TRY(fft_lines<double2>(f, f, lx, *P->fL, -1, 1.0, nullptr, P->st));
+    VIE_TRY(fft_lines<double2>(f, f, lx, *P->fL, -1, 1.0, xsplit.as<double2>(), P->st));
     // y lines: stride L, lines (x, z)
     LineDesc ly{d.Py, d.Py, d.L * d.Pz, d.L, d.Pz, 1, (long long)d.L * d.Py, 0, d.L,
                 1, (long long)d.L * d.Py, 0, d.L};

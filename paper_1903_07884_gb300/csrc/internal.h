@@ -54,7 +54,7 @@ struct BoxPrec {
   DevBuf inv128;             // double2 [nblk][m][m] row-major D_f^{-1} (FP64 path)
   DevBuf rhat64, rhat128;    // [m][n] line-major spectra of the box unknowns
   DevBuf zhat64, zhat128;
-  DevBuf tmp64, tmp128;      // Bluestein scratch [m][M] (non-smooth n only)
+  DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
   const FftLen* fx = nullptr;
 };
 
@@ -77,6 +77,7 @@ struct vie_plan_s {
   vie::DevBuf M128, M64;               // [nz][ny][nx] material M
   vie::DevBuf T128, T64;               // [3][Pz][Py][nx] matvec intermediate
   vie::DevBuf S128, S64;               // [3][Pz][Py][L] full x-spectrum (unfused path only)
+  vie::DevBuf X128, X64;               // split scratch for x-lines longer than shared memory
   vie::DevBuf xin64, xout64;           // c64 staging for vie_matvec / precond (mixed)
   bool has_eps = false;
   bool prec_built = false;

@@ -13,6 +13,8 @@
 // only polls the stop flag between chunks of steps.
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <chrono>
 
@@ -724,7 +726,6 @@ static vie_status norm128(vie_plan_s* P, const double2* v, int idx, double* out)
 vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!P->has_eps) { set_error("vie_solve: permittivity not set"); return VIE_ESTATE; }
-  if (!P->prec_built) VIE_TRY(precond_build(P));
   const bool mixed = P->opts.precision == VIE_MIXED;
   VIE_TRY(krylov_alloc(P, mixed, !mixed));
   Krylov& K = *P->kry;
@@ -740,6 +741,11 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
   VIE_CHECK_LAUNCH();
   double bnorm = 0;
   VIE_TRY(norm128(P, b, 2, &bnorm));
+  if (!std::isfinite(bnorm)) {
+    set_error("vie_solve: non-finite right-hand side (check the permittivity and incident field)");
+    return VIE_EINVAL;
+  }
+  if (!P->prec_built) VIE_TRY(precond_build(P));
   int inner = 0, outer = 0;
   double relres = 0;
   const double tol = P->opts.tol;
@@ -781,6 +787,7 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
       VIE_CHECK_LAUNCH();
       ++outer;
       VIE_TRY(norm128(P, r, 3, &rn));
+      if (!std::isfinite(rn)) { set_error("vie_solve: refinement diverged (non-finite residual)"); return VIE_ECUDA; }
       if (it == 0) break;
       // a step that does not reduce the FP64 residual by 10% (twice in a row)
       // means the inner solve has nothing left to give

@@ -18,6 +18,11 @@ vie_status matvec_alloc(vie_plan_s* P) {
   P->fused_x64 = (size_t)3 * d.L * sizeof(float2) <= 200 * 1024;
   if (!P->fused_x128) VIE_TRY(P->S128.alloc(sizeof(double2) * nS));
   if (!P->fused_x64) VIE_TRY(P->S64.alloc(sizeof(float2) * nS));
+  const int nl = 3 * d.Py * d.Pz;
+  const size_t x128 = P->fused_x128 ? 0 : fft_scratch_elems<double2>(*P->fL, nl);
+  const size_t x64 = P->fused_x64 ? 0 : fft_scratch_elems<float2>(*P->fL, nl);
+  if (x128) VIE_TRY(P->X128.alloc(sizeof(double2) * x128));
+  if (x64) VIE_TRY(P->X64.alloc(sizeof(float2) * x64));
   const long long n3 = 3LL * d.nx * d.ny * d.nz;
   VIE_TRY(P->xin64.alloc(sizeof(float2) * n3));
   VIE_TRY(P->xout64.alloc(sizeof(float2) * n3));

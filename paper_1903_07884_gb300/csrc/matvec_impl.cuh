@@ -292,12 +292,13 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     const int nl = 3 * d.Py * d.Pz;
     LineDesc lf = lines_flat(d.nx, d.L, nl, d.nx, 1, d.L, 1);
     if (!S) { set_error("matvec: missing x-spectrum scratch"); return VIE_EINVAL; }
-    VIE_TRY(fft_lines<C>(T, S, lf, *P->fL, -1, 1.0, nullptr, st));
+    C* X = (C*)(sizeof(C) == 16 ? P->X128.p : P->X64.p);   // split scratch for over-long lines
+    VIE_TRY(fft_lines<C>(T, S, lf, *P->fL, -1, 1.0, X, st));
     { Prof pf_(sizeof(C) == 8 ? "mv_xmul_c64" : "mv_xmul_c128", st); k_mv_xmul<C><<<d.Py * d.Pz, 256, 0, st>>>(S, spec, d); }
     count_launch();
     VIE_CHECK_LAUNCH();
     LineDesc li = lines_flat(d.L, d.nx, nl, d.L, 1, d.nx, 1);
-    VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, nullptr, st));
+    VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, X, st));
   }
   // pass C
   {

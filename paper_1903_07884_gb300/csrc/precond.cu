@@ -287,9 +287,11 @@ __global__ void __launch_bounds__(512) k_block_lu(double2* __restrict__ Aall, in
     for (int kk = 0; kk < nb; ++kk) {
       const int k = k0 + kk;
       double2* col = P + kk * rows;
-      // pivot search over rows k..m-1 (first maximum of |re| + |im|)
+      // pivot search over rows k..m-1 (first maximum of |re| + |im|); the
+      // candidate starts at the diagonal row so that the index stays valid
+      // even if every entry compares false (NaN)
       double best = -1.0;
-      int bi = 0x7fffffff;
+      int bi = kk;
       for (int i = kk + tid; i < rows; i += nt) {
         const double v = cabs1(col[i]);
         if (v > best) { best = v; bi = i; }
@@ -306,9 +308,10 @@ __global__ void __launch_bounds__(512) k_block_lu(double2* __restrict__ Aall, in
         int i0 = ri[0];
         for (int w = 1; w < nw; ++w)
           if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+        if (i0 < kk || i0 >= rows) i0 = kk;
         piv_s = i0;
         piv[k] = k0 + i0;
-        if (b0 == 0.0) atomicExch(info, 1);
+        if (!(b0 > 0.0)) atomicExch(info, 1);   // zero or non-finite pivot
       }
       __syncthreads();
       const int pi = piv_s;
@@ -659,7 +662,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   }
   {
     DevBuf tmp;
-    if (B.fx->bluestein) VIE_TRY(tmp.alloc(sizeof(double2) * (size_t)nl * B.fx->M));
+    const size_t ts = fft_scratch_elems<double2>(*B.fx, nl);
+    if (ts) VIE_TRY(tmp.alloc(sizeof(double2) * ts));
     LineDesc ld = lines_flat(n, n, nl, n, 1, 1, nl);   // out: [f][line]
     VIE_TRY(fft_lines<double2>(coef.as<double2>(), B.lam.as<double2>(), ld, *B.fx, -1, 1.0, tmp.as<double2>(), st));
     VIE_CUDA(cudaStreamSynchronize(st));
@@ -724,7 +728,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
     VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
-    if (B.fx->bluestein) VIE_TRY(B.tmp64.alloc(sizeof(float2) * (size_t)m * B.fx->M));
+    const size_t ts = fft_scratch_elems<float2>(*B.fx, m);
+    if (ts) VIE_TRY(B.tmp64.alloc(sizeof(float2) * ts));
   }
   if (want128) {
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
@@ -736,7 +741,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat128.alloc(sizeof(double2) * (size_t)n * m));
     VIE_TRY(B.zhat128.alloc(sizeof(double2) * (size_t)n * m));
-    if (B.fx->bluestein) VIE_TRY(B.tmp128.alloc(sizeof(double2) * (size_t)m * B.fx->M));
+    const size_t ts = fft_scratch_elems<double2>(*B.fx, m);
+    if (ts) VIE_TRY(B.tmp128.alloc(sizeof(double2) * ts));
   }
   int hinfo = 0;
   VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -746,6 +752,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
 }
 
 vie_status precond_build(vie_plan_s* P) {
+  reset_graphs(P);   // captured Arnoldi steps point at the old blocks
   precond_free(P);
   if (P->opts.precond == VIE_PREC_NONE) { P->prec_built = true; P->kept_fraction = 0; return VIE_OK; }
   const auto t0 = std::chrono::steady_clock::now();

@@ -180,3 +180,51 @@ def test_solve_tiny_cases_match_dense_lu():
             w, info = plan.solve(p.e_inc)
             plan.close()
             assert relerr(w.cpu().numpy(), ref) <= 1e-6, (p.name, prec, info)
+
+
+def test_matvec_fp64_long_line_split():
+    """x-embedding longer than one shared-memory line in FP64 (L = 13122 >
+    12736): the split path against the oracle, element-wise."""
+    cuda_or_fail()
+    nx, ny, nz = 6500, 2, 2
+    eps = inputs.random_permittivity(nz, ny, nx, seed=77)
+    x = inputs.random_field((3, nz, ny, nx), seed=78)
+    ref = _oracle_matvec(nx, ny, nz, 0.025, K0, 1.0, eps, x)
+    plan = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_FP64, precond=vie.VIE_PREC_NONE))
+    plan.set_permittivity(eps)
+    y = plan.matvec(to_device(x), vie.VIE_FP64).cpu().numpy()
+    y32 = plan.matvec(to_device(x), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    assert maxerr(y, ref) <= 1e-12
+    assert relerr(y32, ref) <= 2e-5
+
+
+def test_precond_fp64_long_prime_box_bluestein_split():
+    """Prime box length 6379: Bluestein through a 16384-point transform,
+    split once in FP64 (Chan eigenvalues and the FP64 apply)."""
+    cuda_or_fail()
+    p = inputs.straight_guide(6379, 1, 1, 0.025, 1.55, absorber=300)
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, None, 3, 0.0)
+    r = inputs.random_field((3, p.nz, p.ny, p.nx), seed=31)
+    ref = P.apply(r)
+    plan = Plan.for_problem(p, precision=vie.VIE_FP64, reduce_tol=0.0)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    z = plan.precond(to_device(r), vie.VIE_FP64).cpu().numpy()
+    plan.close()
+    assert relerr(z, ref) <= 1e-11
+
+
+def test_solve_rejects_non_finite_permittivity():
+    cuda_or_fail()
+    p = inputs.straight_guide(16, 4, 2, 0.05, 1.55, absorber=2)
+    eps = p.eps.copy()
+    eps[0, 1, 3] = np.nan
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED)
+    plan.set_permittivity(eps)
+    with pytest.raises(vie.VieError) as e:
+        plan.solve(p.e_inc)
+    assert e.value.status == vie.VIE_EINVAL
+    plan.close()
