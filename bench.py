@@ -423,6 +423,9 @@ def run_gpu(args):
             "profile_ms": {k: round(v[1], 4) for k, v in top[:12]}}
     plan.close()
 
+    if args.serving_n > 0:
+        line["serving"] = run_serving(args.serving_n, args.inflight, args.budget_gb, args.tol, args.fp64_serial_s)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S = OracleSample(p)
         ts = [S.iteration() for _ in range(3)]
@@ -441,6 +444,80 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_limit_s: float):
+    """Replay the first n_req requests of the seeded serving stream (Poisson
+    arrivals, 50/s) against the continuous-batching server; every request is
+    submitted at its arrival time with host buffers and its latency runs from
+    arrival to completion.  The same requests are then solved one by one with
+    the plain FP64 GPU method (time-bounded by fp64_limit_s)."""
+    import numpy as np
+
+    from paper_1903_07884_gb300 import inputs, vie
+    from paper_1903_07884_gb300.solver import make_opts
+
+    reqs = inputs.serving_stream(256)[:n_req]
+    probs = [r.problem() for r in reqs]
+    bufs = []
+    for p in probs:
+        bufs.append((np.ascontiguousarray(p.eps), np.ascontiguousarray(p.e_inc),
+                     np.empty(p.e_inc.shape, dtype=np.complex128)))
+    srv = vie.vie_server_create(int(budget_gb * (1 << 30)), inflight)
+    t0 = time.perf_counter()
+    tickets, t_arr, t_done, status = {}, {}, {}, {}
+    infos = {}
+    nxt = 0
+    while len(t_done) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].t_arrival <= now:
+            p = probs[nxt]
+            eps, e, w = bufs[nxt]
+            opts = make_opts(precision=vie.VIE_MIXED, tol=tol, boxes=p.boxes or None, homog=p.homog)
+            st, t = vie.vie_server_submit(srv, p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, opts, eps.ctypes.data,
+                                          e.ctypes.data, w.ctypes.data)
+            tickets[t] = nxt
+            t_arr[nxt] = reqs[nxt].t_arrival
+            if st != vie.VIE_OK:
+                t_done[nxt] = now
+                status[nxt] = st
+            nxt += 1
+        for t, i in tickets.items():
+            if i in t_done:
+                continue
+            st, info = vie.vie_server_poll(srv, t)
+            if st != vie.VIE_PENDING:
+                t_done[i] = time.perf_counter() - t0
+                status[i] = st
+                infos[i] = info
+        time.sleep(0.0005)
+    vie.vie_server_destroy(srv)
+    lat = [1000.0 * (t_done[i] - t_arr[i]) for i in range(len(reqs))]
+    span = max(t_done.values()) - min(t_arr.values())
+    ok = sum(1 for s in status.values() if s in (vie.VIE_OK, vie.VIE_ENOCONV))
+    out = {"requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "max_inflight": inflight, "budget_gb": budget_gb,
+           "mean_iters": float(np.mean([infos[i].iters_inner for i in infos])) if infos else None,
+           "max_relres": float(max(infos[i].relres for i in infos)) if infos else None}
+    # plain FP64 GPU method, serially, same requests
+    lat64 = []
+    t_start = time.perf_counter()
+    for i, p in enumerate(probs):
+        if time.perf_counter() - t_start > fp64_limit_s:
+            break
+        eps, e, _ = bufs[i]
+        w = np.empty(p.e_inc.shape, dtype=np.complex128)
+        opts = make_opts(precision=vie.VIE_FP64, tol=tol, boxes=p.boxes or None, homog=p.homog)
+        ts = time.perf_counter()
+        plan = vie.vie_plan_create(p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, opts, 0)
+        vie.vie_solve_host(plan, eps.ctypes.data, e.ctypes.data, w.ctypes.data, allow_noconv=True)
+        vie.vie_plan_destroy(plan)
+        lat64.append(1000.0 * (time.perf_counter() - ts))
+    if lat64:
+        out["fp64_serial"] = {"requests": len(lat64), "solves_per_s": len(lat64) / (sum(lat64) / 1000.0),
+                              "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
+                              "note": "each request alone, no queueing; first requests of the same stream"}
+    return out
 
 
 def plan_meta(p, info):
@@ -469,6 +546,10 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-n", type=int, default=16, help="requests of the serving stream to replay (0 = skip)")
+    ap.add_argument("--inflight", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=200.0)
+    ap.add_argument("--fp64-serial-s", type=float, default=30.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -253,7 +253,7 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
       const FftLen* h;
       VIE_TRY(fft_get(len / 2, &h));   // half length used by the split, cached before any capture
     }
-    if (3 * b.ny * b.nz > 1152) { set_error("vie_plan_create: box cross-section too large (m > 1152)"); return VIE_EINVAL; }
+    if (3 * b.ny * b.nz > 864) { set_error("vie_plan_create: box cross-section too large (m = 3 ny nz > 864)"); return VIE_EINVAL; }
   }
   VIE_TRY(fft_get(d.L, &P->fL));
   if (d.L > fft_max_len<float2>() || d.L > fft_max_len<double2>()) {

@@ -24,8 +24,8 @@
 namespace vie {
 
 constexpr int RMAX = 128;      // largest supported restart length
-constexpr int NPART = 608;     // CTAs of the reduction kernels (4 per SM)
-constexpr int RED_THREADS = 256;
+constexpr int NPART = 152;     // CTAs of the reduction kernels (one 1024-thread block per SM)
+constexpr int RED_THREADS = 1024;
 
 struct GmresDev {
   double2 H[(RMAX + 1) * RMAX];   // column j at H[j*(RMAX+1) + i], after rotations
@@ -46,7 +46,9 @@ struct GmresDev {
   int iters;                      // total Arnoldi steps of this state
   int reorth;                     // 1: second Gram-Schmidt pass needed (DGKS test)
   int reorths;                    // second passes taken
-  int pad[1];
+  int arrive_dot;                 // arrival counters of the fused grid reductions
+  int arrive_upd;
+  int pad[3];
   double wnorm0;                  // ||A z|| before orthogonalisation
 };
 
@@ -104,15 +106,110 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
   return t;   // valid in thread 0
 }
 
+// sum of partial[b][i] over b by one warp, reading through L2 (the partials
+// were just written by other blocks); fixed order: lane-strided sums, then a
+// butterfly
+__device__ __forceinline__ double2 warp_sum_partials_cg(const double2* __restrict__ partial, int nparts, int i) {
+  const int lane = threadIdx.x & 31;
+  double2 t = make_double2(0, 0);
+#pragma unroll 4
+  for (int b = lane; b < nparts; b += 32) {
+    const double2 p = __ldcg(partial + (long long)b * (RMAX + 1) + i);
+    t.x += p.x;
+    t.y += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  }
+  return t;
+}
+
+// Called by every thread of a block after it wrote its partials: returns
+// true in the last block to arrive (which then owns the grid reduction) and
+// resets the counter there.
+__device__ __forceinline__ bool last_block(int* counter) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (is_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0;
+  }
+  return is_last;
+}
+
+// Hessenberg column, rotations, residual estimate, stop test.  Run by one
+// whole block: the column and the previous rotations are staged in shared
+// memory, then one thread applies the rotations in sequence.
+__device__ void givens_step(GmresDev* __restrict__ s, double nn) {
+  __shared__ double2 col[RMAX + 1];
+  __shared__ double csv[RMAX];
+  __shared__ double2 snv[RMAX];
+  const int j = s->j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = s->hsum[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) { csv[i] = s->cs[i]; snv[i] = s->sn[i]; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(nn);
+    col[j + 1] = make_double2(hn, 0);
+    for (int i = 0; i < j; ++i) {
+      const double2 a = col[i], b = col[i + 1];
+      const double c = csv[i];
+      const double2 sn = snv[i];
+      // [c s; -conj(s) c] [a; b]
+      col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
+      col[i + 1] = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
+    }
+    const double2 a = col[j];
+    const double b = hn;   // real, >= 0
+    double c;
+    double2 sn;
+    const double aa = sqrt(a.x * a.x + a.y * a.y);
+    if (b == 0.0) { c = 1.0; sn = make_double2(0, 0); }
+    else if (aa == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
+    else {
+      const double r = hypot(aa, b);
+      c = aa / r;
+      // s = a conj(b) / (|a| r), b real
+      sn = make_double2(a.x * b / (aa * r), a.y * b / (aa * r));
+    }
+    s->cs[j] = c;
+    s->sn[j] = sn;
+    col[j] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
+    col[j + 1] = make_double2(0, 0);
+    const double2 gj = s->g[j];
+    // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+    const double2 g1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
+    s->g[j + 1] = g1;
+    s->g[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = sqrt(g1.x * g1.x + g1.y * g1.y);
+    s->resest = res;
+    s->hnext = hn;
+    s->iters += 1;
+    s->k = j + 1;
+    if (res <= s->tol_abs || j + 1 >= s->restart || hn == 0.0) s->done = 1;
+    else s->j = j + 1;
+  }
+  __syncthreads();
+  double2* H = s->H + (long long)j * (RMAX + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i] = col[i];
+}
+
 // partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j.
 // Each thread accumulates DOT_T columns at once, so one pass over its
 // elements serves DOT_T dot products and one block reduction.
 constexpr int DOT_T = 8;
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
-                                                             long long n3, const GmresDev* __restrict__ s,
+                                                             long long n3, GmresDev* __restrict__ s,
                                                              double2* __restrict__ partial, int pass) {
-  __shared__ double2 sh[RED_THREADS / 32][DOT_T];
+  // intra-block sums stay in the accumulator precision: FP64 issues at a small
+  // fraction of the FP32 rate on this part, so only the per-block partial is
+  // widened (once per coefficient)
+  __shared__ typename Acc<C>::T shr[RED_THREADS / 32][DOT_T], shi[RED_THREADS / 32][DOT_T];
   if (s->done || (pass == 1 && !s->reorth)) return;
   const int j = s->j;
   const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
@@ -144,13 +241,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict
         xr += __shfl_xor_sync(0xffffffffu, xr, o);
         xi += __shfl_xor_sync(0xffffffffu, xi, o);
       }
-      if (lane == 0) sh[warp][t] = make_double2((double)xr, (double)xi);
+      if (lane == 0) { shr[warp][t] = xr; shi[warp][t] = xi; }
     }
     __syncthreads();
     if (threadIdx.x < nt) {
-      double2 acc = make_double2(0, 0);
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { acc.x += sh[w2][threadIdx.x].x; acc.y += sh[w2][threadIdx.x].y; }
-      partial[(long long)blockIdx.x * (RMAX + 1) + i0 + threadIdx.x] = acc;
+      T accr = 0, acci = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { accr += shr[w2][threadIdx.x]; acci += shi[w2][threadIdx.x]; }
+      partial[(long long)blockIdx.x * (RMAX + 1) + i0 + threadIdx.x] = make_double2((double)accr, (double)acci);
     }
     __syncthreads();
   }
@@ -158,13 +255,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict
     T nn = 0;
     for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nn += w[e].x * w[e].x + w[e].y * w[e].y;
     for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    if (lane == 0) sh[warp][0] = make_double2((double)nn, 0.0);
+    if (lane == 0) shr[warp][0] = nn;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2][0].x;
-      partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2(t, 0.0);
+      T t = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += shr[w2][0];
+      partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2((double)t, 0.0);
     }
+  }
+  // the last block to finish reduces the partials: h (pass 0 sets, pass 1
+  // adds) and, in pass 0, ||w|| before orthogonalisation
+  GmresDev* sm = const_cast<GmresDev*>(s);
+  if (!last_block(&sm->arrive_dot)) return;
+  const int nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    const double2 t = warp_sum_partials_cg(partial, gridDim.x, i);
+    if (lane == 0) {
+      sm->hc[i] = t;
+      if (pass == 0) sm->hsum[i] = t;
+      else { sm->hsum[i].x += t.x; sm->hsum[i].y += t.y; }
+    }
+  }
+  if (pass == 0 && warp == nw - 1) {
+    const double t = warp_sum_partials_cg(partial, gridDim.x, RMAX).x;
+    if (lane == 0) sm->wnorm0 = sqrt(t);
   }
 }
 
@@ -185,30 +299,10 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__
   return t;
 }
 
-// hc[i] = sum_b partial[b][i]; mode 0: hsum = hc, mode 1: hsum += hc.
-// One warp per coefficient.
-__global__ void k_reduce_h(const double2* __restrict__ partial, GmresDev* __restrict__ s, int nparts, int mode) {
-  if (s->done || (mode == 1 && !s->reorth)) return;
-  const int j = s->j;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (mode == 0 && warp == nw - 1) {
-    const double t = warp_sum_partials(partial, nparts, RMAX).x;
-    if (lane == 0) s->wnorm0 = sqrt(t);
-  }
-  for (int i = warp; i <= j; i += nw) {
-    const double2 t = warp_sum_partials(partial, nparts, i);
-    if (lane == 0) {
-      s->hc[i] = t;
-      if (mode == 0) s->hsum[i] = t;
-      else { s->hsum[i].x += t.x; s->hsum[i].y += t.y; }
-    }
-  }
-}
-
 // w -= sum_i hc[i] V_i ; optionally partial[b][0] = ||w||^2 over the chunk
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V, C* __restrict__ w, long long n3,
-                                                        const GmresDev* __restrict__ s, double2* __restrict__ partial,
+                                                        GmresDev* __restrict__ s, double2* __restrict__ partial,
                                                         int pass) {
   __shared__ double2 sh[32];
   __shared__ C hcs[RMAX + 1];
@@ -243,75 +337,37 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V,
     nrm += x.x * x.x + x.y * x.y;
   }
   if (want_norm) {
+    __shared__ T shn[32];
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sh[warp] = make_double2((double)nrm, 0.0);
+    if (lane == 0) shn[warp] = nrm;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += sh[w2].x;
-      partial[(long long)blockIdx.x * (RMAX + 1)] = make_double2(t, 0.0);
+      T t = 0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += shn[w2];
+      partial[(long long)blockIdx.x * (RMAX + 1)] = make_double2((double)t, 0.0);
     }
   }
-}
-
-// DGKS test after the first Gram-Schmidt pass: re-orthogonalise only if the
-// projection removed more than 1 - 1/sqrt(2) of ||w||
-__global__ void k_reorth_check(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts) {
-  if (s->done) return;
-  const double nn = warp_sum_partials(partial, nparts, 0).x;
-  if (threadIdx.x != 0) return;
-  const int r = sqrt(nn) < 0.70710678118654752 * s->wnorm0 ? 1 : 0;
-  s->reorth = r;
-  s->reorths += r;
-}
-
-// Hessenberg column, rotations, residual estimate, stop test
-__global__ void k_givens(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts) {
-  if (s->done) return;
-  const double nn = warp_sum_partials(partial, nparts, 0).x;
-  if (threadIdx.x != 0) return;
-  const int j = s->j;
-  const double hn = sqrt(nn);
-  double2* col = s->H + (long long)j * (RMAX + 1);
-  for (int i = 0; i <= j; ++i) col[i] = s->hsum[i];
-  col[j + 1] = make_double2(hn, 0);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = col[i], b = col[i + 1];
-    const double c = s->cs[i];
-    const double2 sn = s->sn[i];
-    // [c s; -conj(s) c] [a; b]
-    col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
-    col[i + 1] = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
+  // the last block: ||w|| over the grid, then (pass 0) the DGKS test, and the
+  // Givens step once no second Gram-Schmidt pass follows
+  GmresDev* sm = const_cast<GmresDev*>(s);
+  if (!last_block(&sm->arrive_upd)) return;
+  __shared__ double nn_s;
+  if ((threadIdx.x >> 5) == 0) {
+    const double nn = warp_sum_partials_cg(partial, gridDim.x, 0).x;
+    if (threadIdx.x == 0) nn_s = nn;
   }
-  const double2 a = col[j];
-  const double b = hn;   // real, >= 0
-  double c;
-  double2 sn;
-  const double aa = sqrt(a.x * a.x + a.y * a.y);
-  if (b == 0.0) { c = 1.0; sn = make_double2(0, 0); }
-  else if (aa == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
-  else {
-    const double r = hypot(aa, b);
-    c = aa / r;
-    // s = a conj(b) / (|a| r), b real
-    sn = make_double2(a.x * b / (aa * r), a.y * b / (aa * r));
+  __syncthreads();
+  const double nn = nn_s;
+  bool final_pass = true;
+  if (pass == 0) {
+    // re-orthogonalise only if the projection removed more than 1 - 1/sqrt(2) of ||w||
+    const int r = sqrt(nn) < 0.70710678118654752 * sm->wnorm0 ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) { sm->reorth = r; sm->reorths += r; }
+    final_pass = (r == 0);
   }
-  s->cs[j] = c;
-  s->sn[j] = sn;
-  col[j] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
-  col[j + 1] = make_double2(0, 0);
-  const double2 gj = s->g[j];
-  // g_{j+1} = -conj(s) g_j ; g_j = c g_j
-  s->g[j + 1] = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
-  s->g[j] = make_double2(c * gj.x, c * gj.y);
-  const double res = sqrt(s->g[j + 1].x * s->g[j + 1].x + s->g[j + 1].y * s->g[j + 1].y);
-  s->resest = res;
-  s->hnext = hn;
-  s->iters += 1;
-  s->k = j + 1;
-  if (res <= s->tol_abs || j + 1 >= s->restart || hn == 0.0) s->done = 1;
-  else s->j = j + 1;
+  if (final_pass) givens_step(sm, nn);
 }
 
 // V_{j} = w / h (j already advanced) and u = V_j
@@ -321,7 +377,7 @@ __global__ void k_scale_next(C* __restrict__ V, const C* __restrict__ w, C* __re
   if (s->done) return;
   const int j = s->j;
   using T = typename real_of<C>::type;
-  const T inv = (T)(1.0 / s->hnext);
+  const T inv = (T)1 / (T)s->hnext;   // reciprocal in the vector precision
   C* Vj = V + (long long)j * n3;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     const C v = cscale(w[e], inv);
@@ -354,6 +410,8 @@ __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict
   s->k = 0;
   s->resest = beta;
   s->reorth = 0;
+  s->arrive_dot = 0;
+  s->arrive_upd = 0;
   for (int i = 0; i <= restart; ++i) s->g[i] = make_double2(0, 0);
   s->g[0] = make_double2(beta, 0);
   s->done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
@@ -363,7 +421,7 @@ template <class C>
 __global__ void k_cycle_v0(const C* __restrict__ r, C* __restrict__ V, C* __restrict__ u, long long n3,
                            const GmresDev* __restrict__ s) {
   using T = typename real_of<C>::type;
-  const T inv = s->beta > 0 ? (T)(1.0 / s->beta) : (T)0;
+  const T inv = s->beta > 0 ? (T)1 / (T)s->beta : (T)0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     const C v = cscale(r[e], inv);
     V[e] = v;
@@ -569,20 +627,16 @@ static vie_status enqueue_step(vie_plan_s* P) {
   const long long n3 = K.n3;
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
+  // CGS2 with the DGKS test: dot (+ grid reduction of h in its last block),
+  // update (+ ||w||, DGKS test and, on the final pass, the Givens step in its
+  // last block); the second pass exits at once when not needed
   for (int pass = 0; pass < 2; ++pass) {
     { Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
-    { Prof pf_("arnoldi_reduce", st); k_reduce_h<<<1, 1024, 0, st>>>(part, s, NPART, pass); }
     { Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
-    count_launch(3);
-    if (pass == 0) {
-      Prof pf_("reorth_check", st);
-      k_reorth_check<<<1, 32, 0, st>>>(s, part, NPART);
-      count_launch();
-    }
+    count_launch(2);
   }
-  { Prof pf_("givens", st); k_givens<<<1, 32, 0, st>>>(s, part, NPART); }
   { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s); }
-  count_launch(2);
+  count_launch(1);
   VIE_CHECK_LAUNCH();
   return VIE_OK;
 }

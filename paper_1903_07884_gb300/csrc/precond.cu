@@ -716,9 +716,11 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     count_launch();
     VIE_CHECK_LAUNCH();
   }
-  const int CB = 32;
-  dim3 gi(B.nblk, ceil_div(m, CB));
+  // column chunk of the inverse: m x (CB + 1) elements of shared memory
+  auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 1)); };
   if (want64) {
+    const int CB = chunk(sizeof(float2));
+    dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
     const size_t smem = sizeof(float2) * (size_t)m * (CB + 1);
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -732,6 +734,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     if (ts) VIE_TRY(B.tmp64.alloc(sizeof(float2) * ts));
   }
   if (want128) {
+    const int CB = chunk(sizeof(double2));
+    dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
     const size_t smem = sizeof(double2) * (size_t)m * (CB + 1);
     VIE_CUDA(cudaFuncSetAttribute(k_block_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

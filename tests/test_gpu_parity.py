@@ -113,13 +113,15 @@ def _precond_case(name):
         return inputs.straight_guide(37, 3, 2, 0.05, 1.55, absorber=3), 0.0, 2
     if name == "bragg_boxes_mode":
         return inputs.bragg_grating(96, 12, 4, 0.025, 1.55, wide=8, narrow=6, period=16), 1e-3, 1
+    if name == "wide_box_m576":
+        return inputs.straight_guide(24, 24, 8, 0.025, 1.55, core_ny=16, core_nz=8, absorber=2), 0.0, 3
     if name == "coupler_boxes":
         return inputs.directional_coupler(64, 0.025, 1.55, ny=24, nz=4, core_w=8, gap=4, margin=2), 0.0, 3
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["straight_full", "small_reduced", "prime_nx_bluestein", "bragg_boxes_mode",
-                                  "coupler_boxes"])
+                                  "coupler_boxes", "wide_box_m576"])
 def test_precond_fp64_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
@@ -137,7 +139,7 @@ def test_precond_fp64_matches_oracle(name):
     assert maxerr(z, ref) <= 1e-11
 
 
-@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode"])
+@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode", "wide_box_m576"])
 def test_precond_mixed_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
