@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "VIE solves/s at 1e-6 rel. err (mixed vs FP64 GPU); matvec HBM GB/s; p50/p99 ms"
 UNIT = "solves/s"
-PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP64_PEAK_TFLOPS = 1.196      # DFMA probe on this machine's GB300 (152 SMs at 2.07 GHz)
 FP32_PEAK_TFLOPS = 69.94      # FFMA probe, same run
 
@@ -155,6 +155,9 @@ def algorithmic(kernel: str, p, plan_meta: dict):
     if kernel == "block_gemv_c64":
         m, nh = plan_meta["m"], plan_meta["nhalf"]
         return "hbm", c * nh * m * m
+    if kernel == "rep_gemm_tc":
+        m, nd = plan_meta["m"], plan_meta["ndisc"]
+        return "tensor", 8.0 * nd * m * m              # nd x m x m complex multiply-adds
     if kernel == "block_lu":
         m, nblk = plan_meta["m"], plan_meta["nblk"]
         return "alu", nblk * (8.0 / 3.0) * m ** 3     # complex LU: m^3/3 complex multiply-adds
@@ -393,6 +396,16 @@ def run_gpu(args):
             roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / pk["hbm_gbs"], "traffic": None, "share": tot / total_prof,
                     "avg_launch_ms": avg_ms, "launches": cnt, "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)"}
+        elif kind == "tensor":
+            # tf32 peak = measured sustained bf16 x the nominal tf32 / bf16 ratio (1.1 / 2.25);
+            # the 3xTF32 split issues three MMAs per algorithmic product
+            tf32 = pk["bf16_tflops_sustained"] * 1.1 / 2.25
+            ach = amount / (avg_ms * 1e-3) / 1e12
+            roof = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
+                    "frac": ach / tf32, "traffic": None, "share": tot / total_prof,
+                    "avg_launch_ms": avg_ms, "launches": cnt,
+                    "peak_source": f"{pk_src} (bf16_tflops_sustained x 1.1/2.25 nominal tf32 ratio; 3xTF32 "
+                                   "issues 3 MMAs per algorithmic product)"}
         else:
             ach = amount / (avg_ms * 1e-3) / 1e12
             roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -522,18 +535,20 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
 
 def plan_meta(p, info):
     """Block sizes of the preconditioner for the work formulas: every box of
-    the workloads has the same cross-section, so the stored complex-FP32
-    inverses give the blocks per box (one LU launch per box)."""
+    the workloads has the same cross-section, so the stored block and
+    discarded-slot counts divide evenly over the boxes."""
     boxes = p.boxes or [(0, 0, 0, p.nx, p.ny, p.nz)]
     m = 3 * boxes[0][4] * boxes[0][5]
-    nblk = info["precond_bytes"] / (8.0 * m * m) / len(boxes)
-    nkept = info["kept_fraction"] * sum(b[3] for b in boxes) / len(boxes)
+    nblk = info["precond_blocks"] / len(boxes)
+    ndisc = info["precond_discarded"] / len(boxes)
     # mean (j + 1) over the Arnoldi steps: every refinement step is one
     # restart cycle of at most 50 steps
     its, outer = info["iters_inner"], max(1, info["iters_outer"])
     per = its / outer
     mean_j1 = (per + 1) / 2.0
-    return {"m": m, "nblk": nblk, "nhalf": max(1.0, (nkept + 1) / 2.0), "mean_j1": mean_j1}
+    # the representative takes a slot of its own unless it is kept
+    return {"m": m, "nblk": nblk, "nhalf": max(1.0, nblk - 1), "ndisc": ndisc, "nboxes": len(boxes),
+            "mean_j1": mean_j1}
 
 
 def main():

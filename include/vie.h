@@ -92,6 +92,10 @@ typedef struct {
   double kept_fraction;   /* kept blocks / total frequencies over all boxes          */
   float t_setup_ms;       /* preconditioner build time of the last build             */
   float t_solve_ms;       /* wall time of the last solve                             */
+  long long precond_blocks;    /* stored (inverted) blocks over all boxes: the kept
+                                  frequencies f <= n/2 plus one representative each  */
+  long long precond_discarded; /* frequencies applied with the representative block
+                                  (the discarded ones, Sec. 5.1.1), over all boxes    */
 } vie_info;
 
 typedef struct vie_plan_s* vie_plan_t;

@@ -55,6 +55,7 @@ struct BoxPrec {
   DevBuf rhat64, rhat128;    // [m][n] line-major spectra of the box unknowns
   DevBuf zhat64, zhat128;
   DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
+  DevBuf bpack, apack;       // tensor-core operands of the representative-block product (packed tf32 hi/lo)
   const FftLen* fx = nullptr;
 };
 
@@ -79,10 +80,12 @@ struct vie_plan_s {
   vie::DevBuf S128, S64;               // [3][Pz][Py][L] full x-spectrum (unfused path only)
   vie::DevBuf X128, X64;               // split scratch for x-lines longer than shared memory
   vie::DevBuf xin64, xout64;           // c64 staging for vie_matvec / precond (mixed)
+  vie::DevBuf dev_err;                 // int: set by a kernel whose bounded wait ran out
   bool has_eps = false;
   bool prec_built = false;
   std::vector<std::unique_ptr<vie::BoxPrec>> bp;
   size_t precond_bytes = 0;
+  long long precond_blocks = 0, precond_discarded = 0;
   double kept_fraction = 1.0;
   float t_setup_ms = 0;
   std::unique_ptr<vie::Krylov> kry;

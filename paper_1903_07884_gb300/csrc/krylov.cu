@@ -858,7 +858,14 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
   VIE_TRY(norm128(P, r, 4, &rn));
   relres = bnorm > 0 ? rn / bnorm : 0.0;
   VIE_CUDA(cudaMemcpyAsync(w_out, x, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, st));
+  int herr = 0;
+  VIE_CUDA(cudaMemcpyAsync(&herr, P->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   VIE_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), st);
+    set_error("vie_solve: a tensor-core wait ran out (results invalid)");
+    return VIE_ETIMEOUT;
+  }
   const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) {
     info->iters_inner = inner;
@@ -868,6 +875,8 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
     info->kept_fraction = P->kept_fraction;
     info->t_setup_ms = P->t_setup_ms;
     info->t_solve_ms = ms;
+    info->precond_blocks = P->precond_blocks;
+    info->precond_discarded = P->precond_discarded;
   }
   return relres <= tol ? VIE_OK : VIE_ENOCONV;
 }

@@ -22,6 +22,7 @@
 
 #include "greens.cuh"
 #include "internal.h"
+#include "umma.cuh"
 #include "prof.h"
 
 namespace vie {
@@ -607,6 +608,174 @@ __global__ void __launch_bounds__(256) k_rep_gemm(const C* __restrict__ Drep, co
   }
 }
 
+// Representative-block product on the tensor cores (tcgen05, kind::tf32,
+// accumulator in TMEM), complex FP32 through a real formulation with the
+// real and imaginary parts of each source row p interleaved along K:
+//   C[t][2i + c] = sum_k A[t][k] B[2i + c][k],   k = 2p + c' < 2m,
+//   A[t][2p] = Re R[p][f_t],  A[t][2p+1] = Im R[p][f_t],
+//   B[2i][2p] = Re D[i][p],   B[2i][2p+1] = -Im D[i][p],
+//   B[2i+1][2p] = Im D[i][p], B[2i+1][2p+1] = Re D[i][p],
+// so C's columns are the interleaved real and imaginary parts of Z[i][f_t].
+// Each fp32 operand is split into tf32 hi + lo and the product accumulates
+// hi*hi + hi*lo + lo*hi (FP32-level accuracy).
+//
+// Both operands are packed in global memory in the order the MMA reads them
+// from shared memory (K-major core matrices, chunks of TC_KC along K, hi then
+// lo), so every K-chunk of a tile is one contiguous bulk copy: B once per
+// build, A by a gather kernel per apply.  The GEMM is a TC_STAGES-deep ring:
+// one thread issues the bulk copies, one issues the MMAs, and the commit of a
+// chunk's MMAs frees its stage.
+constexpr int TC_M = 128, TC_N = 64, TC_KC = 32, TC_STAGES = 4;
+constexpr int TC_ACHUNK = 2 * TC_M * TC_KC;   // floats per packed A chunk (hi + lo)
+constexpr int TC_BCHUNK = 2 * TC_N * TC_KC;   // floats per packed B chunk (hi + lo)
+constexpr int TC_STAGE_BYTES = (TC_ACHUNK + TC_BCHUNK) * 4;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES;
+
+// (row, k) of slot q of a K-major core-matrix chunk with TC_KC columns
+__device__ __forceinline__ void tc_slot(int q, int& row, int& k) {
+  row = (q >> 8) * 8 + ((q >> 2) & 7);
+  k = ((q >> 5) & 7) * 4 + (q & 3);
+}
+
+// B operand of one representative block, packed [N tile][chunk][hi | lo]
+__global__ void k_bpack(const float2* __restrict__ D, float* __restrict__ Bp, int m) {
+  const int nchunks = 2 * m / TC_KC;
+  const long long total = (long long)(2 * m / TC_N) * nchunks * (TC_N * TC_KC);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % (TC_N * TC_KC));
+    const long long ct = e / (TC_N * TC_KC);
+    const int nt = (int)(ct / nchunks), c = (int)(ct % nchunks);
+    int row, k;
+    tc_slot(q, row, k);
+    const int nrow = nt * TC_N + row, kg = c * TC_KC + k;
+    const float2 d = D[(long long)(nrow >> 1) * m + (kg >> 1)];
+    const int co = nrow & 1, ci = kg & 1;
+    const float v = co == 0 ? (ci == 0 ? d.x : -d.y) : (ci == 0 ? d.y : d.x);
+    float hi, lo;
+    umma::split_tf32(v, hi, lo);
+    Bp[ct * TC_BCHUNK + q] = hi;
+    Bp[ct * TC_BCHUNK + TC_N * TC_KC + q] = lo;
+  }
+}
+
+// A operand: the discarded frequencies' columns of R (line-major [p][f]),
+// packed [M tile][chunk][hi | lo]; each thread takes one (re, im) pair
+__global__ void k_apack(const float2* __restrict__ R, const int* __restrict__ disc, int ndisc, int m, int n,
+                        float* __restrict__ Ap) {
+  const int nchunks = 2 * m / TC_KC;
+  const long long total = (long long)((ndisc + TC_M - 1) / TC_M) * nchunks * (TC_M * TC_KC / 2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int q = 2 * (int)(e % (TC_M * TC_KC / 2));
+    const long long ct = e / (TC_M * TC_KC / 2);
+    const int mt = (int)(ct / nchunks), c = (int)(ct % nchunks);
+    int row, k;
+    tc_slot(q, row, k);
+    const int t = mt * TC_M + row;
+    const int p = (c * TC_KC + k) >> 1;
+    const float2 v = t < ndisc ? R[(long long)p * n + disc[t]] : make_float2(0.f, 0.f);
+    float2 hi, lo;
+    umma::split_tf32(v.x, hi.x, lo.x);
+    umma::split_tf32(v.y, hi.y, lo.y);
+    *(float2*)(Ap + ct * TC_ACHUNK + q) = hi;
+    *(float2*)(Ap + ct * TC_ACHUNK + TC_M * TC_KC + q) = lo;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_rep_gemm_tc(const float* __restrict__ Ap, const float* __restrict__ Bp,
+                                                     const int* __restrict__ disc, int ndisc,
+                                                     float2* __restrict__ Z, int m, int n, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+  __shared__ uint32_t tslot;
+  __shared__ int failed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int nchunks = 2 * m / TC_KC;
+  const unsigned long long kLimitNs = 1000000000ull;   // 1 s per wait
+  if (warp == 2) umma::tmem_alloc(&tslot, TC_N);
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) { umma::mbar_init(&full[s], 1); umma::mbar_init(&empty[s], 1); }
+    umma::mbar_init(&done, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tslot;
+
+  if (tid == 0) {
+    // producer: chunk c into stage c % TC_STAGES once the MMAs of chunk c - TC_STAGES are done
+    const float* a = Ap + (long long)mt * nchunks * TC_ACHUNK;
+    const float* b = Bp + (long long)nt * nchunks * TC_BCHUNK;
+    int issued = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % TC_STAGES;
+      if (c >= TC_STAGES && !umma::mbar_wait_ns(&empty[s], ((c / TC_STAGES) - 1) & 1, kLimitNs)) {
+        atomicExch(&failed, 1);
+        break;
+      }
+      unsigned char* st = smem + (size_t)s * TC_STAGE_BYTES;
+      umma::mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+      umma::bulk_g2s(st, a + (long long)c * TC_ACHUNK, TC_ACHUNK * 4, &full[s]);
+      umma::bulk_g2s(st + TC_ACHUNK * 4, b + (long long)c * TC_BCHUNK, TC_BCHUNK * 4, &full[s]);
+      issued = c + 1;
+    }
+    // every copy issued must land before the block may exit
+    for (int c = (issued > TC_STAGES ? issued - TC_STAGES : 0); c < issued; ++c)
+      umma::mbar_wait_ns(&full[c % TC_STAGES], (c / TC_STAGES) & 1, kLimitNs);
+  } else if (tid == 32) {
+    // MMA issuer
+    const uint32_t idesc = umma::idesc_tf32(TC_M, TC_N);
+    const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c % TC_STAGES;
+      if (!umma::mbar_wait_ns(&full[s], (c / TC_STAGES) & 1, kLimitNs)) { ok = false; break; }
+      umma::fence_after_sync();
+      const uint32_t base = umma::smem_u32(smem + (size_t)s * TC_STAGE_BYTES);
+      const uint32_t ah = base, al = base + TC_M * TC_KC * 4;
+      const uint32_t bh = base + TC_ACHUNK * 4, bl = bh + TC_N * TC_KC * 4;
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 8; ++ks) {
+        const uint32_t o = ks * 256;
+        umma::mma_tf32(tmem, umma::smem_desc(ah + o, lbo, sbo), umma::smem_desc(bh + o, lbo, sbo), idesc,
+                       (c | ks) ? 1u : 0u);
+        umma::mma_tf32(tmem, umma::smem_desc(ah + o, lbo, sbo), umma::smem_desc(bl + o, lbo, sbo), idesc, 1u);
+        umma::mma_tf32(tmem, umma::smem_desc(al + o, lbo, sbo), umma::smem_desc(bh + o, lbo, sbo), idesc, 1u);
+      }
+      umma::commit(&empty[s]);
+    }
+    if (!ok) atomicExch(&failed, 1);
+    umma::commit(&done);   // tracks every MMA issued above
+  }
+  __syncwarp();
+  const bool ok = umma::mbar_wait_ns(&done, 0, kLimitNs);
+  __syncthreads();
+  if (!ok || failed) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    umma::fence_after_sync();
+    const int t = mt * TC_M + 32 * warp + lane;
+    const int f = t < ndisc ? disc[t] : -1;
+#pragma unroll
+    for (int col0 = 0; col0 < TC_N; col0 += 16) {
+      float v[16];
+      umma::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col0, v);
+      if (f >= 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int io = (nt * TC_N + col0) / 2 + q;
+          Z[(long long)io * n + f] = make_float2(v[2 * q], v[2 * q + 1]);
+        }
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 2) umma::tmem_dealloc(tmem, TC_N);
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -622,6 +791,8 @@ void precond_free(vie_plan_s* P) {
   P->bp.clear();
   P->prec_built = false;
   P->precond_bytes = 0;
+  P->precond_blocks = 0;
+  P->precond_discarded = 0;
 }
 
 static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128) {
@@ -730,6 +901,16 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
     VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
+    // tensor-core operands of the representative-block product (tf32 hi/lo split)
+    if ((2 * m) % TC_N == 0 && B.ndisc > 0) {
+      const long long nch = 2LL * m / TC_KC;
+      VIE_TRY(B.bpack.alloc(sizeof(float) * (size_t)(2 * m / TC_N) * nch * TC_BCHUNK));
+      VIE_TRY(B.apack.alloc(sizeof(float) * (size_t)ceil_div(B.ndisc, TC_M) * nch * TC_ACHUNK));
+      Prof pf_("bpack", st);
+      k_bpack<<<152 * 4, 256, 0, st>>>(B.inv64.as<float2>() + (size_t)B.rep * m * m, B.bpack.as<float>(), m);
+      count_launch();
+      VIE_CHECK_LAUNCH();
+    }
     const size_t ts = fft_scratch_elems<float2>(*B.fx, m);
     if (ts) VIE_TRY(B.tmp64.alloc(sizeof(float2) * ts));
   }
@@ -762,7 +943,7 @@ vie_status precond_build(vie_plan_s* P) {
   const auto t0 = std::chrono::steady_clock::now();
   const bool want64 = P->opts.precision == VIE_MIXED;
   const bool want128 = P->opts.precision == VIE_FP64;
-  long long kept = 0, total = 0;
+  long long kept = 0, total = 0, nblk = 0, ndisc = 0;
   size_t bytes = 0;
   for (const vie_box& b : P->boxes) {
     std::unique_ptr<BoxPrec> B(new BoxPrec());
@@ -770,10 +951,14 @@ vie_status precond_build(vie_plan_s* P) {
     VIE_TRY(build_box(P, *B, want64, want128));
     kept += B->nkept;
     total += B->n;
-    bytes += B->inv64.bytes + B->inv128.bytes;
+    bytes += B->inv64.bytes + B->inv128.bytes + B->bpack.bytes + B->apack.bytes;
+    nblk += B->nblk;
+    ndisc += B->ndisc;
     P->bp.push_back(std::move(B));
   }
   P->precond_bytes = bytes;
+  P->precond_blocks = nblk;
+  P->precond_discarded = ndisc;
   P->kept_fraction = total ? (double)kept / total : 0;
   P->prec_built = true;
   P->t_setup_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -827,7 +1012,22 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
       VIE_CHECK_LAUNCH();
     }
     // discarded frequencies against the representative block
-    if (B.ndisc > 0) {
+    if (B.ndisc > 0 && sizeof(C) == 8 && B.bpack.p) {
+      // tensor cores (tcgen05, 3xTF32): gather + split A, then the pipelined GEMM
+      {
+        Prof pf_("rep_apack", st);
+        k_apack<<<152 * 4, 256, 0, st>>>((const float2*)rh, B.disc.as<int>(), B.ndisc, m, n, B.apack.as<float>());
+        count_launch();
+        VIE_CHECK_LAUNCH();
+      }
+      Prof pf_("rep_gemm_tc", st);
+      VIE_CUDA(cudaFuncSetAttribute(k_rep_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+      dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / TC_N);
+      k_rep_gemm_tc<<<grid, 128, TC_SMEM, st>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(), B.ndisc,
+                                                (float2*)zh, m, n, P->dev_err.as<int>());
+      count_launch();
+      VIE_CHECK_LAUNCH();
+    } else if (B.ndisc > 0) {
       Prof pf_(sizeof(C) == 8 ? "rep_gemm_c64" : "rep_gemm_c128", st);
       dim3 grid(ceil_div(B.ndisc, GB_F), ceil_div(m, GB_I));
       k_rep_gemm<C><<<grid, 256, 0, st>>>(inv + (size_t)B.rep * m * m, B.disc.as<int>(), B.ndisc, rh, zh, m, n);

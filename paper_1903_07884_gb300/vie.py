@@ -38,7 +38,8 @@ class vie_info(ctypes.Structure):
     _fields_ = [("iters_inner", ctypes.c_int), ("iters_outer", ctypes.c_int),
                 ("relres", ctypes.c_double), ("precond_bytes", ctypes.c_size_t),
                 ("kept_fraction", ctypes.c_double), ("t_setup_ms", ctypes.c_float),
-                ("t_solve_ms", ctypes.c_float)]
+                ("t_solve_ms", ctypes.c_float), ("precond_blocks", ctypes.c_longlong),
+                ("precond_discarded", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

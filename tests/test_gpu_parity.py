@@ -156,6 +156,34 @@ def test_precond_mixed_matches_oracle(name):
     assert relerr(z, ref) <= 1e-4
 
 
+def test_precond_mixed_tensor_core_block_product():
+    """The discarded-frequency product with the representative block (Sec. 4.2)
+    runs on the tensor cores in the mixed path (3xTF32 split, FP32-level
+    accuracy): the 16x8 cross-section gives m = 384, and the discarded
+    frequencies fill 128-frequency tiles with a ragged last one."""
+    cuda_or_fail()
+    p = inputs.straight_guide(320, 16, 8, 0.025, 1.55)
+    tau = 1e-3
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, p.boxes, 3, tau)
+    assert 0 < len(P.boxes[0].kept) < p.nx // 2   # most frequencies take the representative block
+    r = inputs.random_field((3, p.nz, p.ny, p.nx), seed=23)
+    ref = P.apply(r)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=tau, homog=3)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    vie.vie_profile_enable(1)
+    vie.vie_profile_reset()
+    z = plan.precond(to_device(r), vie.VIE_MIXED).cpu().numpy()
+    table = vie.profile_table()
+    vie.vie_profile_enable(0)
+    plan.close()
+    assert table.get("rep_gemm_tc", (0, 0.0))[0] == 1, table
+    assert relerr(z, ref) <= 2e-6
+    assert maxerr(z, ref) <= 2e-5
+
+
 @pytest.mark.parametrize("precision,tol,bound", [(vie.VIE_FP64, 1e-11, 1e-7), (vie.VIE_MIXED, 1e-10, 1e-6)])
 def test_solve_small_straight_matches_dense_lu(precision, tol, bound):
     """64x8x4 bar with absorbers: GPU solution against the oracle's direct LU."""
