@@ -158,9 +158,13 @@ def algorithmic(kernel: str, p, plan_meta: dict):
     if kernel == "rep_gemm_tc":
         m, nd = plan_meta["m"], plan_meta["ndisc"]
         return "tensor", 8.0 * nd * m * m              # nd x m x m complex multiply-adds
-    if kernel == "block_lu":
+    if kernel == "lu_update":
+        # trailing updates A22 -= L21 U12 of the blocked LU (panels of 16): 8 real flops per
+        # complex multiply-add, averaged over the panel steps (one launch per step and box)
         m, nblk = plan_meta["m"], plan_meta["nblk"]
-        return "alu", nblk * (8.0 / 3.0) * m ** 3     # complex LU: m^3/3 complex multiply-adds
+        steps = [(k0, min(16, m - k0)) for k0 in range(0, m, 16) if m - k0 - min(16, m - k0) > 0]
+        flops = sum(8.0 * nb * (m - k0 - nb) ** 2 for k0, nb in steps)
+        return "alu", nblk * flops / len(steps)
     return None
 
 
@@ -422,7 +426,8 @@ def run_gpu(args):
                        "preconditioner": "1-level Chan-Olkin, real-mean homogenised, reduction tau=1e-3",
                        "l2": "512 MB buffer written between timed steps (outside the step events)",
                        "parallelism": f"replicas x{world}"},
-            "iters": {"inner": infos[-1]["iters_inner"], "outer": infos[-1]["iters_outer"]},
+            "iters": {"inner": infos[-1]["iters_inner"], "outer": infos[-1]["iters_outer"],
+                      "reorth_passes": infos[-1]["reorth_passes"]},
             "relres_fp64": infos[-1]["relres"], "kept_fraction": infos[-1]["kept_fraction"],
             "precond_bytes": infos[-1]["precond_bytes"],
             "fp64_gpu": {"value": 1000.0 / statistics.mean(t64) if t64 else None, "unit": UNIT,

@@ -96,6 +96,7 @@ typedef struct {
                                   frequencies f <= n/2 plus one representative each  */
   long long precond_discarded; /* frequencies applied with the representative block
                                   (the discarded ones, Sec. 5.1.1), over all boxes    */
+  int reorth_passes;           /* Arnoldi steps that took the second Gram-Schmidt pass */
 } vie_info;
 
 typedef struct vie_plan_s* vie_plan_t;

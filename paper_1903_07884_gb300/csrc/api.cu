@@ -129,6 +129,35 @@ void prof_record(const char* name, cudaStream_t st, cudaEvent_t* e0, cudaEvent_t
 
 }  // namespace vie
 
+namespace vie {
+
+vie_status smem_optin_raw(const void* kern, size_t need) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, int>> done;
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  int limit = -1;
+  for (const auto& d : done)
+    if (d.first.first == dev && d.first.second == kern) limit = d.second;
+  if (limit < 0) {
+    int optin = 0;
+    VIE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    VIE_CUDA(cudaFuncGetAttributes(&fa, kern));
+    limit = optin - (int)fa.sharedSizeBytes;
+    VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    done.push_back({{dev, kern}, limit});
+  }
+  if (need > (size_t)limit) {
+    set_error("kernel needs %zu bytes of shared memory, more than the %d available", need, limit);
+    return VIE_EINVAL;
+  }
+  return VIE_OK;
+}
+
+}  // namespace vie
+
 using namespace vie;
 
 extern "C" {

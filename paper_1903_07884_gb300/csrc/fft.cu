@@ -224,7 +224,7 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
   if (pp) {
     const size_t smem = 2 * (size_t)lpc * line_bytes;
     auto kern = k_fft_lines<C, 0>;
-    if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_TRY(smem_optin(kern, smem));
     Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);
     kern<<<grid, 256, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, pre_stride, pre_off, post, post_mode,
                                   post2, post2_mode, scale);
@@ -241,7 +241,7 @@ static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const Fft
   {                                                                                               \
     auto kern = k_fft_lines<C, ME>;                                                               \
     if (smem > 48 * 1024)                                                                         \
-      VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+      VIE_TRY(smem_optin(kern, smem));                                                                 \
     Prof pf_(sizeof(C) == 8 ? "fft_lines_c64" : "fft_lines_c128", st);                           \
     kern<<<grid, threads, smem, st>>>(in, out, d, p, sign, lpc, pre, pre_mode, pre_stride, pre_off, \
                                       post, post_mode, post2, post2_mode, scale);                \

@@ -198,9 +198,29 @@ __device__ void givens_step(GmresDev* __restrict__ s, double nn) {
   for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i] = col[i];
 }
 
+// Sum of 16 values over a warp as a reduce-scatter butterfly (16 shuffles
+// instead of 5 per value): returns, in every lane, the warp sum of value
+// (lane >> 1) & 15.
+template <class T>
+__device__ __forceinline__ T warp_reduce16(const T (&v)[16], int lane) {
+  T a8[8], a4[4], a2[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a8[k] = (b4 ? v[8 + k] : v[k]) + __shfl_xor_sync(0xffffffffu, b4 ? v[k] : v[8 + k], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a4[k] = (b3 ? a8[4 + k] : a8[k]) + __shfl_xor_sync(0xffffffffu, b3 ? a8[k] : a8[4 + k], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) a2[k] = (b2 ? a4[2 + k] : a4[k]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[k] : a4[2 + k], 4);
+  T a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
+  a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+  return a1;
+}
+
 // partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j.
-// Each thread accumulates DOT_T columns at once, so one pass over its
-// elements serves DOT_T dot products and one block reduction.
+// Each thread accumulates DOT_T = 8 columns at once, so one pass over its
+// elements serves 8 dot products; the 16 real sums are reduced over the warp
+// by a butterfly and over the block by 16 warps at once (one barrier per
+// group: the warp sums alternate between two shared buffers).
 constexpr int DOT_T = 8;
 template <class C>
 __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
@@ -209,58 +229,52 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict
   // intra-block sums stay in the accumulator precision: FP64 issues at a small
   // fraction of the FP32 rate on this part, so only the per-block partial is
   // widened (once per coefficient)
-  __shared__ typename Acc<C>::T shr[RED_THREADS / 32][DOT_T], shi[RED_THREADS / 32][DOT_T];
+  using T = typename Acc<C>::T;
+  __shared__ T ws[2][RED_THREADS / 32][2 * DOT_T];
+  __shared__ T wn[RED_THREADS / 32];
   if (s->done || (pass == 1 && !s->reorth)) return;
   const int j = s->j;
   const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
   const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
-  using T = typename Acc<C>::T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 <= j; i0 += DOT_T) {
-    T ar[DOT_T], ai[DOT_T];
+  double* pb = reinterpret_cast<double*>(partial + (long long)blockIdx.x * (RMAX + 1));
+  T nn = 0;   // ||w||^2 over the chunk (pass 0), gathered with the first group
+  int buf = 0;
+  for (int i0 = 0; i0 <= j; i0 += DOT_T, buf ^= 1) {
+    T a[2 * DOT_T];
 #pragma unroll
-    for (int t = 0; t < DOT_T; ++t) { ar[t] = 0; ai[t] = 0; }
+    for (int t = 0; t < 2 * DOT_T; ++t) a[t] = 0;
     const int nt = min(DOT_T, j + 1 - i0);
+    const bool with_norm = pass == 0 && i0 == 0;
     for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
       const C x = w[e];
+      if (with_norm) nn += x.x * x.x + x.y * x.y;
 #pragma unroll
       for (int t = 0; t < DOT_T; ++t) {
         if (t < nt) {
           const C v = V[(long long)(i0 + t) * n3 + e];
-          ar[t] += v.x * x.x + v.y * x.y;
-          ai[t] += v.x * x.y - v.y * x.x;
+          a[2 * t] += v.x * x.x + v.y * x.y;
+          a[2 * t + 1] += v.x * x.y - v.y * x.x;
         }
       }
     }
-    // warp sums in the accumulator precision (FP64 throughput is low on
-    // this part), block sums in FP64
-#pragma unroll
-    for (int t = 0; t < DOT_T; ++t) {
-      T xr = ar[t], xi = ai[t];
-      for (int o = 16; o > 0; o >>= 1) {
-        xr += __shfl_xor_sync(0xffffffffu, xr, o);
-        xi += __shfl_xor_sync(0xffffffffu, xi, o);
-      }
-      if (lane == 0) { shr[warp][t] = xr; shi[warp][t] = xi; }
-    }
+    const T r = warp_reduce16<T>(a, lane);
+    if ((lane & 1) == 0) ws[buf][warp][lane >> 1] = r;
     __syncthreads();
-    if (threadIdx.x < nt) {
-      T accr = 0, acci = 0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) { accr += shr[w2][threadIdx.x]; acci += shi[w2][threadIdx.x]; }
-      partial[(long long)blockIdx.x * (RMAX + 1) + i0 + threadIdx.x] = make_double2((double)accr, (double)acci);
+    if (warp < 2 * DOT_T) {   // warp q sums value q over the block's warps
+      T x = ws[buf][lane][warp];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && (warp >> 1) < nt) pb[2 * (i0 + (warp >> 1)) + (warp & 1)] = (double)x;
     }
-    __syncthreads();
   }
   if (pass == 0) {   // ||w||^2 before orthogonalisation, slot RMAX
-    T nn = 0;
-    for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nn += w[e].x * w[e].x + w[e].y * w[e].y;
     for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    if (lane == 0) shr[warp][0] = nn;
+    if (lane == 0) wn[warp] = nn;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      T t = 0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += shr[w2][0];
-      partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2((double)t, 0.0);
+    if (warp == 0) {
+      T x = wn[lane];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2((double)x, 0.0);
     }
   }
   // the last block to finish reduces the partials: h (pass 0 sets, pass 1
@@ -318,14 +332,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V,
   for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
     C x = w[e];
     int i = 0;
-    for (; i + 3 <= j; i += 4) {
-      const C v0 = V[(long long)i * n3 + e], v1 = V[(long long)(i + 1) * n3 + e];
-      const C v2 = V[(long long)(i + 2) * n3 + e], v3 = V[(long long)(i + 3) * n3 + e];
-      const C h0 = hcs[i], h1 = hcs[i + 1], h2 = hcs[i + 2], h3 = hcs[i + 3];
-      x.x -= h0.x * v0.x - h0.y * v0.y; x.y -= h0.x * v0.y + h0.y * v0.x;
-      x.x -= h1.x * v1.x - h1.y * v1.y; x.y -= h1.x * v1.y + h1.y * v1.x;
-      x.x -= h2.x * v2.x - h2.y * v2.y; x.y -= h2.x * v2.y + h2.y * v2.x;
-      x.x -= h3.x * v3.x - h3.y * v3.y; x.y -= h3.x * v3.y + h3.y * v3.x;
+    for (; i + 7 <= j; i += 8) {
+      C v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = V[(long long)(i + t) * n3 + e];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const C h = hcs[i + t];
+        x.x -= h.x * v[t].x - h.y * v[t].y;
+        x.y -= h.x * v[t].y + h.y * v[t].x;
+      }
     }
     for (; i <= j; ++i) {
       const C v = V[(long long)i * n3 + e];
@@ -800,6 +816,8 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
     return VIE_EINVAL;
   }
   if (!P->prec_built) VIE_TRY(precond_build(P));
+  GmresDev* sdev = K.state.as<GmresDev>();
+  VIE_CUDA(cudaMemsetAsync(&sdev->reorths, 0, sizeof(int), st));
   int inner = 0, outer = 0;
   double relres = 0;
   const double tol = P->opts.tol;
@@ -858,8 +876,9 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
   VIE_TRY(norm128(P, r, 4, &rn));
   relres = bnorm > 0 ? rn / bnorm : 0.0;
   VIE_CUDA(cudaMemcpyAsync(w_out, x, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, st));
-  int herr = 0;
+  int herr = 0, hreorth = 0;
   VIE_CUDA(cudaMemcpyAsync(&herr, P->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaMemcpyAsync(&hreorth, &sdev->reorths, sizeof(int), cudaMemcpyDeviceToHost, st));
   VIE_CUDA(cudaStreamSynchronize(st));
   if (herr) {
     cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), st);
@@ -877,6 +896,7 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
     info->t_solve_ms = ms;
     info->precond_blocks = P->precond_blocks;
     info->precond_discarded = P->precond_discarded;
+    info->reorth_passes = hreorth;
   }
   return relres <= tol ? VIE_OK : VIE_ENOCONV;
 }

@@ -229,8 +229,7 @@ static inline int threads_for(long long E, int& maxe, int cap_per) {
 
 template <class K>
 static vie_status set_smem(K kern, size_t smem) {
-  if (smem > 48 * 1024) VIE_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return VIE_OK;
+  return smem_optin(kern, smem);
 }
 
 #define VIE_DISPATCH_MAXE(ME, CALL)                                             \

@@ -258,15 +258,19 @@ __global__ void k_block_assemble(double2* __restrict__ D, const double2* __restr
 }
 
 // ---------------------------------------------------------------------------
-// 5a. batched FP64 LU with partial pivoting (column-major, one block per
-//     matrix, right-looking with panels of NB columns).
+// 5a. batched FP64 LU with partial pivoting (column-major, right-looking with
+//     panels of NB columns).  Each panel step is two launches over all
+//     matrices: the panel (pivoting, row swaps, U12 = L11^-1 A12; one block per
+//     matrix), then the trailing update A22 -= L21 U12 as 32x32 tiles of every
+//     matrix, so that the FP64 work fills every SM whatever the batch size.
 // ---------------------------------------------------------------------------
 constexpr int LU_NB = 16;
+constexpr int LU_TILE = 32;
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 
-__global__ void __launch_bounds__(512) k_block_lu(double2* __restrict__ Aall, int* __restrict__ pivall, int m,
-                                                  int* __restrict__ info) {
+__global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, int* __restrict__ pivall, int m,
+                                                  int k0, int* __restrict__ info) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* P = reinterpret_cast<double2*>(smem_raw);     // panel: NB columns x (m - k0) rows
   __shared__ double rv[32];
@@ -276,128 +280,157 @@ __global__ void __launch_bounds__(512) k_block_lu(double2* __restrict__ Aall, in
   int* piv = pivall + (long long)blockIdx.x * m;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int k0 = 0; k0 < m; k0 += LU_NB) {
-    const int nb = min(LU_NB, m - k0);
-    const int rows = m - k0;
-    // load panel
-    for (int e = tid; e < nb * rows; e += nt) {
-      const int j = e / rows, i = e - j * rows;
-      P[j * rows + i] = A[(long long)(k0 + j) * m + k0 + i];
+  const int nb = min(LU_NB, m - k0);
+  const int rows = m - k0;
+  for (int e = tid; e < nb * rows; e += nt) {
+    const int j = e / rows, i = e - j * rows;
+    P[j * rows + i] = A[(long long)(k0 + j) * m + k0 + i];
+  }
+  __syncthreads();
+  for (int kk = 0; kk < nb; ++kk) {
+    const int k = k0 + kk;
+    double2* col = P + kk * rows;
+    // pivot search over rows k..m-1 (first maximum of |re| + |im|); the
+    // candidate starts at the diagonal row so that the index stays valid
+    // even if every entry compares false (NaN)
+    double best = -1.0;
+    int bi = kk;
+    for (int i = kk + tid; i < rows; i += nt) {
+      const double v = cabs1(col[i]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b0 = rv[0];
+      int i0 = ri[0];
+      for (int w = 1; w < nw; ++w)
+        if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+      if (i0 < kk || i0 >= rows) i0 = kk;
+      piv_s = i0;
+      piv[k] = k0 + i0;
+      if (!(b0 > 0.0)) atomicExch(info, 1);   // zero or non-finite pivot
     }
     __syncthreads();
+    const int pi = piv_s;
+    if (pi != kk) {   // swap rows kk and pi inside the panel
+      for (int j = tid; j < nb; j += nt) {
+        const double2 t = P[j * rows + kk];
+        P[j * rows + kk] = P[j * rows + pi];
+        P[j * rows + pi] = t;
+      }
+    }
+    __syncthreads();
+    const double2 pv = col[kk];
+    const double2 ipv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0, 0) : cinv(pv);
+    for (int i = kk + 1 + tid; i < rows; i += nt) col[i] = cmul(col[i], ipv);
+    __syncthreads();
+    // rank-1 update of the remaining panel columns
+    const int rem = nb - kk - 1;
+    for (int e = tid; e < rem * (rows - kk - 1); e += nt) {
+      const int jj = kk + 1 + e / (rows - kk - 1);
+      const int i = kk + 1 + e % (rows - kk - 1);
+      double2 a = P[jj * rows + i];
+      const double2 l = col[i], u = P[jj * rows + kk];
+      a.x -= l.x * u.x - l.y * u.y;
+      a.y -= l.x * u.y + l.y * u.x;
+      P[jj * rows + i] = a;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * rows; e += nt) {
+    const int j = e / rows, i = e - j * rows;
+    A[(long long)(k0 + j) * m + k0 + i] = P[j * rows + i];
+  }
+  // the panel's row swaps on every other column (left: the final L; right:
+  // the columns still to be factored), then U12 = L11^{-1} A12
+  for (int j = tid; j < m; j += nt) {
+    if (j >= k0 && j < k0 + nb) continue;
+    double2* cj = A + (long long)j * m;
     for (int kk = 0; kk < nb; ++kk) {
-      const int k = k0 + kk;
-      double2* col = P + kk * rows;
-      // pivot search over rows k..m-1 (first maximum of |re| + |im|); the
-      // candidate starts at the diagonal row so that the index stays valid
-      // even if every entry compares false (NaN)
-      double best = -1.0;
-      int bi = kk;
-      for (int i = kk + tid; i < rows; i += nt) {
-        const double v = cabs1(col[i]);
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double b0 = rv[0];
-        int i0 = ri[0];
-        for (int w = 1; w < nw; ++w)
-          if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
-        if (i0 < kk || i0 >= rows) i0 = kk;
-        piv_s = i0;
-        piv[k] = k0 + i0;
-        if (!(b0 > 0.0)) atomicExch(info, 1);   // zero or non-finite pivot
-      }
-      __syncthreads();
-      const int pi = piv_s;
-      // swap rows kk and pi inside the panel
-      if (pi != kk) {
-        for (int j = tid; j < nb; j += nt) {
-          const double2 t = P[j * rows + kk];
-          P[j * rows + kk] = P[j * rows + pi];
-          P[j * rows + pi] = t;
+      const int k = k0 + kk, p = piv[k];
+      if (p != k) { const double2 t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
+    }
+    if (j >= k0 + nb) {
+      double2 u[LU_NB];
+#pragma unroll
+      for (int t = 0; t < LU_NB; ++t) u[t] = t < nb ? cj[k0 + t] : make_double2(0, 0);
+#pragma unroll
+      for (int t = 0; t < LU_NB; ++t) {
+        if (t >= nb) break;
+#pragma unroll
+        for (int i = t + 1; i < LU_NB; ++i) {
+          if (i >= nb) break;
+          const double2 l = P[t * rows + i];
+          u[i].x -= l.x * u[t].x - l.y * u[t].y;
+          u[i].y -= l.x * u[t].y + l.y * u[t].x;
         }
       }
-      __syncthreads();
-      const double2 pv = col[kk];
-      const double2 ipv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0, 0) : cinv(pv);
-      for (int i = kk + 1 + tid; i < rows; i += nt) col[i] = cmul(col[i], ipv);
-      __syncthreads();
-      // rank-1 update of the remaining panel columns
-      const int rem = nb - kk - 1;
-      for (int e = tid; e < rem * (rows - kk - 1); e += nt) {
-        const int jj = kk + 1 + e / (rows - kk - 1);
-        const int i = kk + 1 + e % (rows - kk - 1);
-        double2 a = P[jj * rows + i];
-        const double2 l = col[i], u = P[jj * rows + kk];
-        a.x -= l.x * u.x - l.y * u.y;
-        a.y -= l.x * u.y + l.y * u.x;
-        P[jj * rows + i] = a;
-      }
-      __syncthreads();
-    }
-    // store panel
-    for (int e = tid; e < nb * rows; e += nt) {
-      const int j = e / rows, i = e - j * rows;
-      A[(long long)(k0 + j) * m + k0 + i] = P[j * rows + i];
-    }
-    // apply the panel's row swaps to the other columns
-    for (int j = tid; j < m; j += nt) {
-      if (j >= k0 && j < k0 + nb) continue;
-      double2* cj = A + (long long)j * m;
-      for (int kk = 0; kk < nb; ++kk) {
-        const int k = k0 + kk, p = piv[k];
-        if (p != k) { const double2 t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
-      }
-    }
-    __syncthreads();
-    const int right = m - k0 - nb;
-    if (right > 0) {
-      // U12 = L11^{-1} A12 (unit lower triangular), one column per thread
-      for (int j = k0 + nb + tid; j < m; j += nt) {
-        double2* cj = A + (long long)j * m + k0;
-        double2 u[LU_NB];
 #pragma unroll
-        for (int t = 0; t < LU_NB; ++t) u[t] = t < nb ? cj[t] : make_double2(0, 0);
-#pragma unroll
-        for (int t = 0; t < LU_NB; ++t) {
-          if (t >= nb) break;
-#pragma unroll
-          for (int i = t + 1; i < LU_NB; ++i) {
-            if (i >= nb) break;
-            const double2 l = P[t * rows + i];
-            u[i].x -= l.x * u[t].x - l.y * u[t].y;
-            u[i].y -= l.x * u[t].y + l.y * u[t].x;
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < LU_NB; ++t) if (t < nb) cj[t] = u[t];
-      }
-      __syncthreads();
-      // A22 -= L21 U12: thread per element, i fastest (coalesced columns)
-      const int r22 = m - k0 - nb;
-      for (long long e = tid; e < (long long)r22 * right; e += nt) {
-        const int jj = (int)(e / r22), ii = (int)(e - (long long)jj * r22);
-        const int j = k0 + nb + jj, i = k0 + nb + ii;
-        double2* cj = A + (long long)j * m;
-        double2 a = cj[i];
-#pragma unroll 4
-        for (int t = 0; t < nb; ++t) {
-          const double2 l = P[t * rows + nb + ii];
-          const double2 u = cj[k0 + t];
-          a.x -= l.x * u.x - l.y * u.y;
-          a.y -= l.x * u.y + l.y * u.x;
-        }
-        cj[i] = a;
-      }
+      for (int t = 0; t < LU_NB; ++t) if (t < nb) cj[k0 + t] = u[t];
     }
-    __syncthreads();
+  }
+}
+
+// A22 -= L21 U12 on one 32x32 tile of one matrix, with three real products
+// per complex product (T1 = Lr Ur, T2 = Li Ui, T3 = (Lr + Li)(Ur + Ui);
+// re -= T1 - T2, im -= T3 - T1 - T2): FP64 issues slowly on this part, and
+// this saves a quarter of the multiply-adds.  Thread (tx, ty) owns rows
+// tx, tx + 16 and columns ty, ty + 16 of the tile.
+__global__ void __launch_bounds__(256) k_lu_update(double2* __restrict__ Aall, int m, int k0, int nb) {
+  __shared__ double Lr[LU_NB][LU_TILE], Li[LU_NB][LU_TILE], Ls[LU_NB][LU_TILE];
+  __shared__ double Ur[LU_NB][LU_TILE], Ui[LU_NB][LU_TILE], Us[LU_NB][LU_TILE];
+  const int r0 = k0 + nb;                    // first row / column of A22
+  const int r22 = m - r0;
+  const int nti = (r22 + LU_TILE - 1) / LU_TILE;
+  const int i0 = r0 + (blockIdx.x % nti) * LU_TILE, j0 = r0 + (blockIdx.x / nti) * LU_TILE;
+  double2* A = Aall + (long long)blockIdx.y * m * m;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < LU_NB * LU_TILE; e += blockDim.x) {
+    const int t = e / LU_TILE, q = e % LU_TILE;
+    double2 l = make_double2(0, 0), u = make_double2(0, 0);
+    if (t < nb && i0 + q < m) l = A[(long long)(k0 + t) * m + i0 + q];   // L21[i][t], column k0 + t
+    if (t < nb && j0 + q < m) u = A[(long long)(j0 + q) * m + k0 + t];   // U12[t][j], row k0 + t
+    Lr[t][q] = l.x; Li[t][q] = l.y; Ls[t][q] = l.x + l.y;
+    Ur[t][q] = u.x; Ui[t][q] = u.y; Us[t][q] = u.x + u.y;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  double t1[2][2] = {}, t2[2][2] = {}, t3[2][2] = {};
+  for (int t = 0; t < nb; ++t) {
+    double lr[2], li[2], ls[2], ur[2], ui[2], us[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      lr[a] = Lr[t][tx + 16 * a]; li[a] = Li[t][tx + 16 * a]; ls[a] = Ls[t][tx + 16 * a];
+      ur[a] = Ur[t][ty + 16 * a]; ui[a] = Ui[t][ty + 16 * a]; us[a] = Us[t][ty + 16 * a];
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        t1[a][b] = fma(lr[a], ur[b], t1[a][b]);
+        t2[a][b] = fma(li[a], ui[b], t2[a][b]);
+        t3[a][b] = fma(ls[a], us[b], t3[a][b]);
+      }
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int j = j0 + ty + 16 * b;
+    if (j >= m) continue;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int i = i0 + tx + 16 * a;
+      if (i >= m) continue;
+      double2 v = A[(long long)j * m + i];
+      v.x -= t1[a][b] - t2[a][b];
+      v.y -= t3[a][b] - t1[a][b] - t2[a][b];
+      A[(long long)j * m + i] = v;
+    }
   }
 }
 
@@ -881,11 +914,23 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   // 5. FP64 LU, then the inverse(s)
   {
     const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
-    VIE_CUDA(cudaFuncSetAttribute(k_block_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    Prof pf_("block_lu", st);
-    k_block_lu<<<B.nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, info.as<int>());
-    count_launch();
-    VIE_CHECK_LAUNCH();
+    VIE_TRY(smem_optin(k_lu_panel, smem));
+    for (int k0 = 0; k0 < m; k0 += LU_NB) {
+      const int nb = std::min(LU_NB, m - k0);
+      {
+        Prof pf_("lu_panel", st);
+        k_lu_panel<<<B.nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, k0, info.as<int>());
+        count_launch();
+      }
+      const int r22 = m - k0 - nb;
+      if (r22 > 0) {
+        const int nti = ceil_div(r22, LU_TILE);
+        Prof pf_("lu_update", st);
+        k_lu_update<<<dim3(nti * nti, B.nblk), 256, 0, st>>>(LU.as<double2>(), m, k0, nb);
+        count_launch();
+      }
+      VIE_CHECK_LAUNCH();
+    }
   }
   // column chunk of the inverse: m x (CB + 1) elements of shared memory
   auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 1)); };
@@ -894,7 +939,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
     const size_t smem = sizeof(float2) * (size_t)m * (CB + 1);
-    VIE_CUDA(cudaFuncSetAttribute(k_block_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_TRY(smem_optin(k_block_inv<float2>, smem));
     { Prof pf_("block_inv_c64", st);
       k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB); }
     count_launch();
@@ -919,7 +964,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
     const size_t smem = sizeof(double2) * (size_t)m * (CB + 1);
-    VIE_CUDA(cudaFuncSetAttribute(k_block_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_TRY(smem_optin(k_block_inv<double2>, smem));
     { Prof pf_("block_inv_c128", st);
       k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB); }
     count_launch();
@@ -1021,7 +1066,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
         VIE_CHECK_LAUNCH();
       }
       Prof pf_("rep_gemm_tc", st);
-      VIE_CUDA(cudaFuncSetAttribute(k_rep_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+      VIE_TRY(smem_optin(k_rep_gemm_tc, TC_SMEM));
       dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / TC_N);
       k_rep_gemm_tc<<<grid, 128, TC_SMEM, st>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(), B.ndisc,
                                                 (float2*)zh, m, n, P->dev_err.as<int>());

@@ -43,6 +43,16 @@ void set_error(const char* fmt, ...);
     if (s_ < 0) return s_;                                                      \
   } while (0)
 
+// Let a kernel use the device's whole opt-in dynamic shared memory (less its
+// static shared memory) and check that `need` bytes fit.  Every caller sets
+// the same value, so a plan built on another host thread can never lower the
+// limit under a launch in flight.  Cached per device and kernel.
+vie_status smem_optin_raw(const void* kern, size_t need);
+template <class K>
+inline vie_status smem_optin(K* kern, size_t need) {
+  return need <= 48 * 1024 ? VIE_OK : smem_optin_raw((const void*)kern, need);
+}
+
 // ---------------------------------------------------------------------------
 // complex types
 // ---------------------------------------------------------------------------
