@@ -556,6 +556,22 @@ def plan_meta(p, info):
             "mean_j1": mean_j1}
 
 
+def run_profile_case(args):
+    """Build and solve the workload once in mixed precision: the launch
+    sequence of one bench step, without the timing, comparison and serving
+    legs, so that an ncu capture of it stays short."""
+    from paper_1903_07884_gb300 import vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+    p, wname = workload(args.workload)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, tol=args.tol)
+    plan.set_permittivity(to_device(p.eps))
+    _, info = plan.solve(to_device(p.e_inc))
+    plan.close()
+    print(json.dumps({"profile_case": wname, "iters": info["iters_inner"], "relres": info["relres"],
+                      "launches": vie.vie_kernel_launches()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,7 +586,11 @@ def main():
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=200.0)
     ap.add_argument("--fp64-serial-s", type=float, default=30.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -172,18 +172,26 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
   const int l0 = blockIdx.x * lpc;
   const int nl = min(lpc, d.nlines - l0);
   const int E = nl * n;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    int li, i;
+  auto split = [&](int e, int& li, int& i) {
     if (d.ies == 1) { li = e / n; i = e - li * n; } else { i = e / nl; li = e - i * nl; }
-    const int l = l0 + li;
-    C v = czero<C>();
-    if (i < d.n_in) {
-      const long long off = line_in_off(d, l) + (long long)i * d.ies;
-      v = in[off];
-      if (pre_mode) { C w = pre[i * pre_stride + pre_off]; if (pre_mode == 2) w.y = -w.y; v = cmul(v, w); }
-    }
-    s[li * pitch + i] = v;
-  }
+  };
+  batched_copy<8>(
+      E,
+      [&](int e) {
+        int li, i;
+        split(e, li, i);
+        C v = czero<C>();
+        if (i < d.n_in) {
+          v = in[line_in_off(d, l0 + li) + (long long)i * d.ies];
+          if (pre_mode) { C w = pre[i * pre_stride + pre_off]; if (pre_mode == 2) w.y = -w.y; v = cmul(v, w); }
+        }
+        return v;
+      },
+      [&](int e, C v) {
+        int li, i;
+        split(e, li, i);
+        s[li * pitch + i] = v;
+      });
   __syncthreads();
   SmemLines L{nl, nl, pitch, 0, 1, 0};
   C* res = s;

@@ -56,6 +56,28 @@ inline void fft_plan_finalize(FftPlanDev& p) {
   }
 }
 
+// Element-wise copy of E items by the block, U items per thread at a time:
+// the U loads (load(e), global memory) are all issued before the first store
+// (store(e, v), usually shared memory), so a thread keeps U requests in flight
+// instead of waiting out the memory latency once per item.
+template <int U, class F, class G>
+__device__ __forceinline__ void batched_copy(int E, F load, G store) {
+  using V = decltype(load(0));
+  for (int e0 = threadIdx.x; e0 < E; e0 += U * blockDim.x) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < E) v[u] = load(e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < E) store(e, v[u]);
+    }
+  }
+}
+
 // Lines in shared memory: line l = l1 + nl1 * l2 (l1 < nl1) starts at
 // l1*ls1 + l2*ls2 and holds element i at offset i*es.
 struct SmemLines {

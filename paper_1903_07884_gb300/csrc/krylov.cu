@@ -20,6 +20,7 @@
 
 #include "internal.h"
 #include "prof.h"
+#include "umma.cuh"
 
 namespace vie {
 
@@ -27,37 +28,43 @@ constexpr int RMAX = 128;      // largest supported restart length
 constexpr int NPART = 152;     // CTAs of the reduction kernels (one 1024-thread block per SM)
 constexpr int RED_THREADS = 1024;
 
+constexpr int PST = 2 * (RMAX + 1);   // per-block stride of the reduction partials
+
 struct GmresDev {
   double2 H[(RMAX + 1) * RMAX];   // column j at H[j*(RMAX+1) + i], after rotations
+  double2 Hr[(RMAX + 1) * RMAX];  // the same columns before rotations (Arnoldi relation)
   double cs[RMAX];
   double2 sn[RMAX];
   double2 g[RMAX + 1];
   double2 y[RMAX];
-  double2 hc[RMAX + 1];           // coefficients of the current projection step
-  double2 hsum[RMAX + 1];         // accumulated column (both CGS passes)
+  double2 cs_s[RMAX + 1];         // update coefficients of the current step: s (re-orthogonalisation
+  double2 cs_c[RMAX + 1];         //   of u_j) and c (projection of w)
+  double2 cu;                     // coefficient of u_j in the projection of w
+  double inv_beta;                // 1 / ||u_j - Q s||
+  double nu;                      // ||w''|| of the last update: h_{j,j-1} before its correction
   double beta;                    // norm of the cycle's starting residual
-  double tol_abs;                 // stop when |g_{j+1}| <= tol_abs
-  double hnext;                   // h_{j+1,j}
-  double resest;                  // |g_{j+1}|
-  int j;                          // current column
-  int k;                          // columns in the finished cycle
+  double tol_abs;                 // stop when |g_k| <= tol_abs
+  double hnext;                   // scale of the next basis vector
+  double resest;                  // |g_k|
+  int j;                          // current step
+  int k;                          // final columns of the finished cycle
   int done;                       // 1: cycle finished (converged, full, or breakdown)
   int restart;
-  int iters;                      // total Arnoldi steps of this state
-  int reorth;                     // 1: second Gram-Schmidt pass needed (DGKS test)
-  int reorths;                    // second passes taken
+  int iters;                      // Arnoldi columns formed by this state
+  int reorth;                     // unused (kept for the layout of older callers)
+  int reorths;                    // re-orthogonalised vectors
   int arrive_dot;                 // arrival counters of the fused grid reductions
   int arrive_upd;
   int pad[3];
-  double wnorm0;                  // ||A z|| before orthogonalisation
 };
 
 struct Krylov {
   int restart = 0;
   long long n3 = 0;
-  DevBuf V64, V128;               // (restart + 1) * n3 basis
+  long long ld = 0;               // column stride of the basis (n3 rounded up to 32)
+  DevBuf V64, V128;               // (restart + 1) * ld basis
   DevBuf u64, u128, z64, z128, w64, w128;
-  DevBuf partial;                 // double2 [NPART][RMAX + 1]
+  DevBuf partial;                 // double2 [NPART][PST]
   DevBuf state;                   // GmresDev
   DevBuf x128, r128, b128, d64, rhs64, r64, t128;
   DevBuf scal;                    // double [8]: norms
@@ -114,7 +121,7 @@ __device__ __forceinline__ double2 warp_sum_partials_cg(const double2* __restric
   double2 t = make_double2(0, 0);
 #pragma unroll 4
   for (int b = lane; b < nparts; b += 32) {
-    const double2 p = __ldcg(partial + (long long)b * (RMAX + 1) + i);
+    const double2 p = __ldcg(partial + (long long)b * PST + i);
     t.x += p.x;
     t.y += p.y;
   }
@@ -141,21 +148,66 @@ __device__ __forceinline__ bool last_block(int* counter) {
   return is_last;
 }
 
-// Hessenberg column, rotations, residual estimate, stop test.  Run by one
-// whole block: the column and the previous rotations are staged in shared
-// memory, then one thread applies the rotations in sequence.
-__device__ void givens_step(GmresDev* __restrict__ s, double nn) {
+// As givens_column, run by one warp (lane 0 takes the sequential chain), so
+// that the rest of the block can work meanwhile.
+__device__ void givens_column_warp(GmresDev* __restrict__ s, int jc) {
+  __shared__ double2 colw[RMAX + 1];
+  __shared__ double csw[RMAX];
+  __shared__ double2 snw[RMAX];
+  const int lane = threadIdx.x & 31;
+  const double2* hr = s->Hr + (long long)jc * (RMAX + 1);
+  for (int i = lane; i <= jc + 1; i += 32) colw[i] = hr[i];
+  for (int i = lane; i < jc; i += 32) { csw[i] = s->cs[i]; snw[i] = s->sn[i]; }
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = 0; i < jc; ++i) {
+      const double2 a = colw[i], b = colw[i + 1];
+      const double c = csw[i];
+      const double2 sn = snw[i];
+      colw[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
+      colw[i + 1] = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
+    }
+    const double2 a = colw[jc];
+    const double2 bb = colw[jc + 1];
+    const double b = sqrt(bb.x * bb.x + bb.y * bb.y);
+    double c;
+    double2 sn;
+    const double aa = sqrt(a.x * a.x + a.y * a.y);
+    if (b == 0.0) { c = 1.0; sn = make_double2(0, 0); }
+    else if (aa == 0.0) { c = 0.0; sn = make_double2(1.0, 0.0); }
+    else {
+      const double r = hypot(aa, b);
+      c = aa / r;
+      sn = make_double2(a.x * b / (aa * r), a.y * b / (aa * r));
+    }
+    s->cs[jc] = c;
+    s->sn[jc] = sn;
+    colw[jc] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
+    colw[jc + 1] = make_double2(0, 0);
+    const double2 gj = s->g[jc];
+    const double2 g1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
+    s->g[jc + 1] = g1;
+    s->g[jc] = make_double2(c * gj.x, c * gj.y);
+    s->resest = sqrt(g1.x * g1.x + g1.y * g1.y);
+  }
+  __syncwarp();
+  double2* H = s->H + (long long)jc * (RMAX + 1);
+  for (int i = lane; i <= jc + 1; i += 32) H[i] = colw[i];
+}
+
+// Rotations for the final raw column jc (rows 0..jc+1 in Hr): apply the
+// earlier rotations, form rotation jc, update g and the residual estimate,
+// store the rotated column in H.  Run by one whole block.
+__device__ void givens_column(GmresDev* __restrict__ s, int jc) {
   __shared__ double2 col[RMAX + 1];
   __shared__ double csv[RMAX];
   __shared__ double2 snv[RMAX];
-  const int j = s->j;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = s->hsum[i];
-  for (int i = threadIdx.x; i < j; i += blockDim.x) { csv[i] = s->cs[i]; snv[i] = s->sn[i]; }
+  const double2* hr = s->Hr + (long long)jc * (RMAX + 1);
+  for (int i = threadIdx.x; i <= jc + 1; i += blockDim.x) col[i] = hr[i];
+  for (int i = threadIdx.x; i < jc; i += blockDim.x) { csv[i] = s->cs[i]; snv[i] = s->sn[i]; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double hn = sqrt(nn);
-    col[j + 1] = make_double2(hn, 0);
-    for (int i = 0; i < j; ++i) {
+    for (int i = 0; i < jc; ++i) {
       const double2 a = col[i], b = col[i + 1];
       const double c = csv[i];
       const double2 sn = snv[i];
@@ -163,8 +215,9 @@ __device__ void givens_step(GmresDev* __restrict__ s, double nn) {
       col[i] = make_double2(c * a.x + (sn.x * b.x - sn.y * b.y), c * a.y + (sn.x * b.y + sn.y * b.x));
       col[i + 1] = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
     }
-    const double2 a = col[j];
-    const double b = hn;   // real, >= 0
+    const double2 a = col[jc];
+    const double2 bb = col[jc + 1];
+    const double b = sqrt(bb.x * bb.x + bb.y * bb.y);   // the subdiagonal is real and >= 0
     double c;
     double2 sn;
     const double aa = sqrt(a.x * a.x + a.y * a.y);
@@ -176,26 +229,38 @@ __device__ void givens_step(GmresDev* __restrict__ s, double nn) {
       // s = a conj(b) / (|a| r), b real
       sn = make_double2(a.x * b / (aa * r), a.y * b / (aa * r));
     }
-    s->cs[j] = c;
-    s->sn[j] = sn;
-    col[j] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
-    col[j + 1] = make_double2(0, 0);
-    const double2 gj = s->g[j];
-    // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+    s->cs[jc] = c;
+    s->sn[jc] = sn;
+    col[jc] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
+    col[jc + 1] = make_double2(0, 0);
+    const double2 gj = s->g[jc];
+    // g_{jc+1} = -conj(s) g_jc ; g_jc = c g_jc
     const double2 g1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
-    s->g[j + 1] = g1;
-    s->g[j] = make_double2(c * gj.x, c * gj.y);
-    const double res = sqrt(g1.x * g1.x + g1.y * g1.y);
-    s->resest = res;
-    s->hnext = hn;
-    s->iters += 1;
-    s->k = j + 1;
-    if (res <= s->tol_abs || j + 1 >= s->restart || hn == 0.0) s->done = 1;
-    else s->j = j + 1;
+    s->g[jc + 1] = g1;
+    s->g[jc] = make_double2(c * gj.x, c * gj.y);
+    s->resest = sqrt(g1.x * g1.x + g1.y * g1.y);
   }
   __syncthreads();
-  double2* H = s->H + (long long)j * (RMAX + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i] = col[i];
+  double2* H = s->H + (long long)jc * (RMAX + 1);
+  for (int i = threadIdx.x; i <= jc + 1; i += blockDim.x) H[i] = col[i];
+  __syncthreads();
+}
+
+// sum of partial[b][i] over b by one warp (fixed order: lane-strided sums,
+// then a butterfly)
+__device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__ partial, int nparts, int i) {
+  const int lane = threadIdx.x & 31;
+  double2 t = make_double2(0, 0);
+  for (int b = lane; b < nparts; b += 32) {
+    const double2 p = partial[(long long)b * PST + i];
+    t.x += p.x;
+    t.y += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  }
+  return t;
 }
 
 // Sum of 16 values over a warp as a reduce-scatter butterfly (16 shuffles
@@ -216,185 +281,434 @@ __device__ __forceinline__ T warp_reduce16(const T (&v)[16], int lane) {
   return a1;
 }
 
-// partial[b][i] = sum over this block's chunk of conj(V_i) w, i = 0..j.
-// Each thread accumulates DOT_T = 8 columns at once, so one pass over its
-// elements serves 8 dot products; the 16 real sums are reduced over the warp
-// by a butterfly and over the block by 16 warps at once (one barrier per
-// group: the warp sums alternate between two shared buffers).
-constexpr int DOT_T = 8;
+// ---------------------------------------------------------------------------
+// Streaming Arnoldi passes.  The basis (columns of stride ld, a multiple of
+// 32 elements) is read through bulk asynchronous copies into a ring of
+// ST_STAGES shared-memory tiles: one producer thread issues the copies and 16
+// consumer warps do the arithmetic, so every SM keeps up to ST_STAGES tiles
+// in flight.  Each block owns a contiguous range of the vector cut into
+// sub-chunks of at most ST_TILE bytes; per sub-chunk the tiles are w (the
+// vector being orthogonalised) then V_0 .. V_j.  Every wait is bounded; a wait
+// that runs out sets *err and the block stops consuming.
+// ---------------------------------------------------------------------------
+constexpr int ST_STAGES = 8;
+constexpr int ST_TILE = 16384;                  // bytes per tile
+constexpr int ST_CONS = 512;                    // consumer threads (warps 1..16)
+constexpr int ST_THREADS = ST_CONS + 32;
+constexpr int UPD_THREADS = ST_THREADS + 32;   // k_update: + one warp for the Hessenberg bookkeeping
+constexpr unsigned long long ST_LIMIT_NS = 1000000000ull;
+
+struct StreamGeom {
+  long long c0, c1;   // the block's element range
+  int nsub, sc;       // sub-chunks and elements per sub-chunk (multiple of 32)
+};
+
 template <class C>
-__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const C* __restrict__ V, const C* __restrict__ w,
-                                                             long long n3, GmresDev* __restrict__ s,
-                                                             double2* __restrict__ partial, int pass) {
-  // intra-block sums stay in the accumulator precision: FP64 issues at a small
-  // fraction of the FP32 rate on this part, so only the per-block partial is
-  // widened (once per coefficient)
+__device__ __forceinline__ StreamGeom stream_geom(long long n3) {
+  const long long per = ((n3 + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  StreamGeom g;
+  g.c0 = min(n3, (long long)blockIdx.x * per);
+  g.c1 = min(n3, g.c0 + per);
+  const int maxe = ST_TILE / (int)sizeof(C);
+  g.nsub = (int)((g.c1 - g.c0 + maxe - 1) / maxe);
+  g.sc = g.nsub > 0 ? (int)(((g.c1 - g.c0 + g.nsub - 1) / g.nsub + 31) / 32 * 32) : 0;
+  return g;
+}
+
+struct StreamRing {
+  uint64_t full[ST_STAGES], empty[ST_STAGES];
+};
+
+__device__ __forceinline__ void ring_init(StreamRing& r) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < ST_STAGES; ++i) {
+      umma::mbar_init(&r.full[i], 1);
+      umma::mbar_init(&r.empty[i], ST_CONS / 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// Producer (thread 0): for every sub-chunk, the w tile, the V_j tile, then
+// V_0 .. V_{j-1}, in the order the consumers take them.
+template <class C>
+__device__ void stream_produce(StreamRing& r, unsigned char* tiles, const C* __restrict__ V, long long ld,
+                               const C* __restrict__ w, int j, const StreamGeom& g, int* err) {
+  int tt = 0;
+  bool ok = true;
+  for (int sb = 0; sb < g.nsub && ok; ++sb) {
+    const long long start = g.c0 + (long long)sb * g.sc;
+    const long long cnt = min((long long)g.sc, g.c1 - start);
+    const uint32_t bytes = (uint32_t)(((cnt + 31) / 32 * 32) * sizeof(C));
+    for (int q = 0; q <= j + 1; ++q, ++tt) {
+      const int st = tt % ST_STAGES;
+      if (tt >= ST_STAGES && !umma::mbar_wait_ns(&r.empty[st], ((tt / ST_STAGES) - 1) & 1, ST_LIMIT_NS)) {
+        ok = false;
+        atomicExch(err, 1);
+        break;
+      }
+      // order: w, u_j = V_j, V_0 .. V_{j-1}
+      const C* src = q == 0 ? w + start : V + (long long)(q == 1 ? j : q - 2) * ld + start;
+      umma::mbar_arrive_expect_tx(&r.full[st], bytes);
+      umma::bulk_g2s(tiles + (size_t)st * ST_TILE, src, bytes, &r.full[st]);
+    }
+  }
+  // every copy issued must land before the block may exit
+  for (int t = (tt > ST_STAGES ? tt - ST_STAGES : 0); t < tt; ++t)
+    umma::mbar_wait_ns(&r.full[t % ST_STAGES], (t / ST_STAGES) & 1, ST_LIMIT_NS);
+}
+
+// Consumer side: wait for tile tt, hand its elements to f, release it.
+template <class C, class F>
+__device__ __forceinline__ bool stream_take(StreamRing& r, const unsigned char* tiles, int tt, bool ok, F f, int* err) {
+  const int st = tt % ST_STAGES;
+  if (ok && !umma::mbar_wait_ns(&r.full[st], (tt / ST_STAGES) & 1, ST_LIMIT_NS)) {
+    ok = false;
+    if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+  }
+  if (ok) f(reinterpret_cast<const C*>(tiles + (size_t)st * ST_TILE));
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(&r.empty[st])) : "memory");
+  return ok;
+}
+
+// Delayed classical Gram-Schmidt with re-orthogonalisation (one global
+// reduction and one update per Arnoldi step).  Step j enters with Q = [q_0 ..
+// q_{j-1}] final and u_j = V_j, which step j-1 orthogonalised once and scaled
+// by nu = ||w''||, and with w = A P^{-1} u_j.  One pass over the basis gives
+//   s = Q^H u_j, alpha = u_j^H u_j, z = Q^H w, zeta = u_j^H w;
+// then q_j = (u_j - Q s) / beta with beta^2 = alpha - |s|^2, the previous
+// column is final (h_{:,j-1} += nu s, h_{j,j-1} = nu beta), and, writing
+// t = (zeta - s^H z) / beta, the projection of A P^{-1} q_j is
+//   h_{:,j} = ([z; t] - H_{0:j,0:j-1} s) / beta,
+//   w'' = (w - Q (z - s t / beta) - u_j t / beta) / beta,
+// by the Arnoldi relation A P^{-1} Q = Q_{j+1} H.  The update pass forms q_j
+// and w'' together; u_{j+1} = w'' / ||w''|| is orthogonalised again (its s)
+// at step j + 1.  Column j thus becomes final one step later, so the
+// residual estimate lags by one step; at restart length a last reduction
+// (step j = restart) only finalises the last column.
+//
+// Reduction: tiles per sub-chunk are w, u_j = V_j, then V_0 .. V_{j-1}; a
+// consumer keeps its elements of w and u_j in registers and accumulates four
+// columns (two complex dots each) at a time, reduced over the warp by a
+// butterfly into the warp's row of shared memory.  Partials per block:
+// [i] = (s_i or alpha at i = j), [RMAX + 1 + i] = (z_i or zeta at i = j).
+template <class C>
+__global__ void __launch_bounds__(ST_THREADS) k_dot_partial(const C* __restrict__ V, long long ld,
+                                                            const C* __restrict__ w, long long n3,
+                                                            GmresDev* __restrict__ s, double2* __restrict__ partial,
+                                                            int* __restrict__ err) {
   using T = typename Acc<C>::T;
-  __shared__ T ws[2][RED_THREADS / 32][2 * DOT_T];
-  __shared__ T wn[RED_THREADS / 32];
-  if (s->done || (pass == 1 && !s->reorth)) return;
+  constexpr int KPT = ST_TILE / (int)sizeof(C) / ST_CONS;   // elements per consumer thread per tile
+  constexpr int ROW = 4 * (RMAX + 1) + 4;                    // per warp: s (2 per column), z (2), alpha, zeta
+  extern __shared__ __align__(128) unsigned char tiles[];
+  __shared__ StreamRing ring;
+  if (s->done) return;
   const int j = s->j;
-  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
+  const StreamGeom g = stream_geom<C>(n3);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* pb = reinterpret_cast<double*>(partial + (long long)blockIdx.x * (RMAX + 1));
-  T nn = 0;   // ||w||^2 over the chunk (pass 0), gathered with the first group
-  int buf = 0;
-  for (int i0 = 0; i0 <= j; i0 += DOT_T, buf ^= 1) {
-    T a[2 * DOT_T];
+  T* wsum = reinterpret_cast<T*>(tiles + (size_t)ST_STAGES * ST_TILE);   // [16][ROW]
+  ring_init(ring);
+  if (warp == 0) {
+    if (lane == 0) stream_produce<C>(ring, tiles, V, ld, w, j, g, err);
+  } else {
+    const int ct = threadIdx.x - 32;
+    T* my = wsum + (size_t)(warp - 1) * ROW;
+    for (int i = lane; i < ROW; i += 32) my[i] = 0;
+    __syncwarp();
+    T al = 0, zr = 0, zi = 0;
+    bool ok = true;
+    int tt = 0;
+    for (int sb = 0; sb < g.nsub; ++sb) {
+      const long long start = g.c0 + (long long)sb * g.sc;
+      const int cnt = (int)min((long long)g.sc, g.c1 - start);
+      C xw[KPT], xu[KPT];
+      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
 #pragma unroll
-    for (int t = 0; t < 2 * DOT_T; ++t) a[t] = 0;
-    const int nt = min(DOT_T, j + 1 - i0);
-    const bool with_norm = pass == 0 && i0 == 0;
-    for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
-      const C x = w[e];
-      if (with_norm) nn += x.x * x.x + x.y * x.y;
+        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xw[q] = e < cnt ? t[e] : czero<C>(); }
+      }, err);
+      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
 #pragma unroll
-      for (int t = 0; t < DOT_T; ++t) {
-        if (t < nt) {
-          const C v = V[(long long)(i0 + t) * n3 + e];
-          a[2 * t] += v.x * x.x + v.y * x.y;
-          a[2 * t + 1] += v.x * x.y - v.y * x.x;
+        for (int q = 0; q < KPT; ++q) {
+          const int e = ct + q * ST_CONS;
+          xu[q] = e < cnt ? t[e] : czero<C>();
+          al += xu[q].x * xu[q].x + xu[q].y * xu[q].y;
+          zr += xu[q].x * xw[q].x + xu[q].y * xw[q].y;
+          zi += xu[q].x * xw[q].y - xu[q].y * xw[q].x;
+        }
+      }, err);
+      for (int i0 = 0; i0 < j; i0 += 4) {
+        T a[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) a[q] = 0;
+        const int nt = min(4, j - i0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (t < nt) {
+            ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* tile) {
+#pragma unroll
+              for (int q = 0; q < KPT; ++q) {
+                const int e = ct + q * ST_CONS;
+                if (e < cnt) {
+                  const C v = tile[e];
+                  a[4 * t + 0] += v.x * xu[q].x + v.y * xu[q].y;
+                  a[4 * t + 1] += v.x * xu[q].y - v.y * xu[q].x;
+                  a[4 * t + 2] += v.x * xw[q].x + v.y * xw[q].y;
+                  a[4 * t + 3] += v.x * xw[q].y - v.y * xw[q].x;
+                }
+              }
+            }, err);
+          }
+        }
+        const T r = warp_reduce16<T>(a, lane);
+        const int q = lane >> 1, col = i0 + (q >> 2), part = q & 3;
+        if ((lane & 1) == 0 && (q >> 2) < nt) my[(part < 2 ? 0 : 2 * (RMAX + 1)) + 2 * col + (part & 1)] += r;
+        __syncwarp();
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      al += __shfl_xor_sync(0xffffffffu, al, o);
+      zr += __shfl_xor_sync(0xffffffffu, zr, o);
+      zi += __shfl_xor_sync(0xffffffffu, zi, o);
+    }
+    if (lane == 0) { my[4 * (RMAX + 1)] = al; my[4 * (RMAX + 1) + 1] = zr; my[4 * (RMAX + 1) + 2] = zi; }
+  }
+  __syncthreads();
+  // block sums over the consumer warps, widened to FP64 once per value
+  double* pb = reinterpret_cast<double*>(partial + (long long)blockIdx.x * PST);
+  for (int v = threadIdx.x; v < 4 * j + 3; v += blockDim.x) {
+    int src, dst;
+    if (v < 2 * j) { src = v; dst = v; }                                        // s
+    else if (v < 4 * j) { src = 2 * (RMAX + 1) + (v - 2 * j); dst = src; }     // z
+    else { src = 4 * (RMAX + 1) + (v - 4 * j); dst = v == 4 * j ? 2 * j : 2 * (RMAX + 1) + 2 * j + (v - 4 * j - 1); }
+    T t = 0;
+    for (int w2 = 0; w2 < ST_CONS / 32; ++w2) t += wsum[(size_t)w2 * ROW + src];
+    pb[dst] = (double)t;
+    if (v == 4 * j) pb[2 * j + 1] = 0.0;
+  }
+  // the last block: coefficients, the final column j - 1 and its rotation,
+  // the stop test, and the tentative column j
+  GmresDev* sm = const_cast<GmresDev*>(s);
+  if (!last_block(&sm->arrive_dot)) return;
+  __shared__ double2 sv[RMAX + 1], zv[RMAX + 1];
+  __shared__ double sc_beta, sc_t[2];
+  const int nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    // s_i and z_i together: every lane keeps all its loads in flight
+    double2 a = make_double2(0, 0), b = make_double2(0, 0);
+    double2 pa[(NPART + 31) / 32], pz[(NPART + 31) / 32];
+#pragma unroll
+    for (int q = 0; q < (NPART + 31) / 32; ++q) {
+      const int bk = lane + 32 * q;
+      pa[q] = bk < (int)gridDim.x ? __ldcg(partial + (long long)bk * PST + i) : make_double2(0, 0);
+      pz[q] = bk < (int)gridDim.x ? __ldcg(partial + (long long)bk * PST + RMAX + 1 + i) : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < (NPART + 31) / 32; ++q) { a.x += pa[q].x; a.y += pa[q].y; b.x += pz[q].x; b.y += pz[q].y; }
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+      b.x += __shfl_xor_sync(0xffffffffu, b.x, o);
+      b.y += __shfl_xor_sync(0xffffffffu, b.y, o);
+    }
+    if (lane == 0) { sv[i] = a; zv[i] = b; }
+  }
+  __syncthreads();
+  // beta^2 = alpha - |s|^2 (warp 0) and s^H z (warp 1), lane-strided with a
+  // butterfly: FP64 issues slowly here, so no long single-thread chains
+  if (warp == 0) {
+    double ss = 0;
+    for (int i = lane; i < j; i += 32) ss += sv[i].x * sv[i].x + sv[i].y * sv[i].y;
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    // u_j is already orthogonal to Q up to rounding, so |s|^2 << alpha
+    if (lane == 0) sc_beta = sqrt(fmax(sv[j].x - ss, 1e-12 * sv[j].x));
+  } else if (warp == 1) {
+    double tr = 0, ti = 0;
+    for (int i = lane; i < j; i += 32) {
+      tr += sv[i].x * zv[i].x + sv[i].y * zv[i].y;
+      ti += sv[i].x * zv[i].y - sv[i].y * zv[i].x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      ti += __shfl_xor_sync(0xffffffffu, ti, o);
+    }
+    if (lane == 0) { sc_t[0] = zv[j].x - tr; sc_t[1] = zv[j].y - ti; }
+  }
+  __syncthreads();
+  const double beta = sc_beta;
+  const double2 t = make_double2(sc_t[0] / beta, sc_t[1] / beta);   // t = (zeta - s^H z) / beta
+  if (j > 0) {   // column j - 1 becomes final: h_{:,j-1} += nu s, h_{j,j-1} = nu beta
+    const double nu = sm->nu;
+    double2* hp = sm->Hr + (long long)(j - 1) * (RMAX + 1);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) { hp[i].x += nu * sv[i].x; hp[i].y += nu * sv[i].y; }
+    if (threadIdx.x == 0) hp[j] = make_double2(nu * beta, 0.0);
+  }
+  __syncthreads();
+  // tentative column j: rows 0..j of ([z; t] - H_{0:j,0:j-1} s) / beta, one
+  // warp per row, lanes over the columns
+  for (int r = warp; r <= j; r += nw) {
+    double ar = 0, ai = 0;
+    for (int l = max(r - 1, 0) + lane; l < j; l += 32) {   // H[r][l] = 0 for r > l + 1
+      const double2 h = sm->Hr[(long long)l * (RMAX + 1) + r];
+      ar += h.x * sv[l].x - h.y * sv[l].y;
+      ai += h.x * sv[l].y + h.y * sv[l].x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+      const double2 zr = r < j ? zv[r] : t;
+      sm->Hr[(long long)j * (RMAX + 1) + r] = make_double2((zr.x - ar) / beta, (zr.y - ai) / beta);
+    }
+  }
+  // update coefficients: s, c = z - s t / beta, cu = t / beta, 1 / beta; the
+  // rotation of column j - 1 (a sequential chain) and the stop test run beside
+  // the update (k_update, block 0), off this kernel's critical path
+  const double2 tb = make_double2(t.x / beta, t.y / beta);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    sm->cs_s[i] = sv[i];
+    sm->cs_c[i] = make_double2(zv[i].x - (sv[i].x * tb.x - sv[i].y * tb.y), zv[i].y - (sv[i].x * tb.y + sv[i].y * tb.x));
+  }
+  if (threadIdx.x == 0) {
+    sm->cu = tb;
+    sm->inv_beta = 1.0 / beta;
+    sm->reorths += (j > 0) ? 1 : 0;
+  }
+}
+
+// Hessenberg bookkeeping of step j, run by one warp of block 0 of k_update
+// while the other warps stream: the rotation of the now final column j - 1
+// and the stop test on the residual estimate it gives.
+__device__ void hessenberg_side(GmresDev* __restrict__ s, int j) {
+  if (j == 0) return;
+  givens_column_warp(s, j - 1);
+  if ((threadIdx.x & 31) == 0) {
+    s->k = j;
+    if (s->resest <= s->tol_abs || j >= s->restart) s->done = 1;
+  }
+}
+
+// q_j = (u_j - Q s) / beta into V_j and w'' = (w - Q c - cu u_j) / beta into
+// w, streamed like the reduction (tiles w, u_j, V_0 .. V_{j-1}); then ||w''||
+// as h_{j+1,j} (tentative) and the scale of u_{j+1}.
+template <class C>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(C* __restrict__ V, long long ld, C* __restrict__ w,
+                                                       long long n3, GmresDev* __restrict__ s,
+                                                       double2* __restrict__ partial, int* __restrict__ err) {
+  using T = typename Acc<C>::T;
+  constexpr int KPT = ST_TILE / (int)sizeof(C) / ST_CONS;
+  extern __shared__ __align__(128) unsigned char tiles[];
+  __shared__ StreamRing ring;
+  __shared__ C sco[RMAX + 1], cco[RMAX + 1];
+  __shared__ T shn[UPD_THREADS / 32];
+  if (s->done) return;
+  const int j = s->j;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) { sco[i] = cconv<C>(s->cs_s[i]); cco[i] = cconv<C>(s->cs_c[i]); }
+  const C cu = cconv<C>(s->cu);
+  using R = typename real_of<C>::type;
+  const R ib = (R)s->inv_beta;
+  const StreamGeom g = stream_geom<C>(n3);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ring_init(ring);   // (its barrier also publishes the coefficients)
+  T nrm = 0;
+  if (warp == 0) {
+    if (lane == 0) stream_produce<C>(ring, tiles, V, ld, w, j, g, err);
+  } else if (warp == ST_THREADS / 32) {
+    if (blockIdx.x == 0) hessenberg_side(const_cast<GmresDev*>(s), j);
+  } else {
+    const int ct = threadIdx.x - 32;
+    C* Vj = V + (long long)j * ld;
+    bool ok = true;
+    int tt = 0;
+    for (int sb = 0; sb < g.nsub; ++sb) {
+      const long long start = g.c0 + (long long)sb * g.sc;
+      const int cnt = (int)min((long long)g.sc, g.c1 - start);
+      C xw[KPT], xu[KPT], as[KPT], ac[KPT];
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) { as[q] = czero<C>(); ac[q] = czero<C>(); }
+      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xw[q] = e < cnt ? t[e] : czero<C>(); }
+      }, err);
+      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xu[q] = e < cnt ? t[e] : czero<C>(); }
+      }, err);
+      for (int i = 0; i < j; ++i) {
+        const C hs = sco[i], hc = cco[i];
+        ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* tile) {
+#pragma unroll
+          for (int q = 0; q < KPT; ++q) {
+            const int e = ct + q * ST_CONS;
+            if (e < cnt) {
+              const C v = tile[e];
+              cfma(as[q], hs, v);
+              cfma(ac[q], hc, v);
+            }
+          }
+        }, err);
+      }
+#pragma unroll
+      for (int q = 0; q < KPT; ++q) {
+        const int e = ct + q * ST_CONS;
+        if (e < cnt) {
+          const C qj = cmake<C>((xu[q].x - as[q].x) * ib, (xu[q].y - as[q].y) * ib);
+          C x = csub(xw[q], ac[q]);
+          x.x -= cu.x * xu[q].x - cu.y * xu[q].y;
+          x.y -= cu.x * xu[q].y + cu.y * xu[q].x;
+          x.x *= ib;
+          x.y *= ib;
+          Vj[start + e] = qj;
+          w[start + e] = x;
+          nrm += x.x * x.x + x.y * x.y;
         }
       }
     }
-    const T r = warp_reduce16<T>(a, lane);
-    if ((lane & 1) == 0) ws[buf][warp][lane >> 1] = r;
-    __syncthreads();
-    if (warp < 2 * DOT_T) {   // warp q sums value q over the block's warps
-      T x = ws[buf][lane][warp];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0 && (warp >> 1) < nt) pb[2 * (i0 + (warp >> 1)) + (warp & 1)] = (double)x;
-    }
   }
-  if (pass == 0) {   // ||w||^2 before orthogonalisation, slot RMAX
-    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    if (lane == 0) wn[warp] = nn;
-    __syncthreads();
-    if (warp == 0) {
-      T x = wn[lane];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) partial[(long long)blockIdx.x * (RMAX + 1) + RMAX] = make_double2((double)x, 0.0);
-    }
-  }
-  // the last block to finish reduces the partials: h (pass 0 sets, pass 1
-  // adds) and, in pass 0, ||w|| before orthogonalisation
-  GmresDev* sm = const_cast<GmresDev*>(s);
-  if (!last_block(&sm->arrive_dot)) return;
-  const int nw = blockDim.x >> 5;
-  for (int i = warp; i <= j; i += nw) {
-    const double2 t = warp_sum_partials_cg(partial, gridDim.x, i);
-    if (lane == 0) {
-      sm->hc[i] = t;
-      if (pass == 0) sm->hsum[i] = t;
-      else { sm->hsum[i].x += t.x; sm->hsum[i].y += t.y; }
-    }
-  }
-  if (pass == 0 && warp == nw - 1) {
-    const double t = warp_sum_partials_cg(partial, gridDim.x, RMAX).x;
-    if (lane == 0) sm->wnorm0 = sqrt(t);
-  }
-}
-
-// sum of partial[b][i] over b by one warp (fixed order: lane-strided sums,
-// then a butterfly)
-__device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__ partial, int nparts, int i) {
-  const int lane = threadIdx.x & 31;
-  double2 t = make_double2(0, 0);
-  for (int b = lane; b < nparts; b += 32) {
-    const double2 p = partial[(long long)b * (RMAX + 1) + i];
-    t.x += p.x;
-    t.y += p.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
-    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
-  }
-  return t;
-}
-
-// w -= sum_i hc[i] V_i ; optionally partial[b][0] = ||w||^2 over the chunk
-template <class C>
-__global__ void __launch_bounds__(RED_THREADS) k_update(const C* __restrict__ V, C* __restrict__ w, long long n3,
-                                                        GmresDev* __restrict__ s, double2* __restrict__ partial,
-                                                        int pass) {
-  __shared__ double2 sh[32];
-  __shared__ C hcs[RMAX + 1];
-  if (s->done || (pass == 1 && !s->reorth)) return;
-  const int want_norm = 1;
-  const int j = s->j;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) hcs[i] = cconv<C>(s->hc[i]);
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (lane == 0) shn[warp] = nrm;
   __syncthreads();
-  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
-  const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
-  using T = typename Acc<C>::T;
-  T nrm = 0;
-  for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
-    C x = w[e];
-    int i = 0;
-    for (; i + 7 <= j; i += 8) {
-      C v[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = V[(long long)(i + t) * n3 + e];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const C h = hcs[i + t];
-        x.x -= h.x * v[t].x - h.y * v[t].y;
-        x.y -= h.x * v[t].y + h.y * v[t].x;
-      }
-    }
-    for (; i <= j; ++i) {
-      const C v = V[(long long)i * n3 + e];
-      const C h = hcs[i];
-      x.x -= h.x * v.x - h.y * v.y;
-      x.y -= h.x * v.y + h.y * v.x;
-    }
-    w[e] = x;
-    nrm += x.x * x.x + x.y * x.y;
+  if (threadIdx.x == 0) {
+    T t = 0;
+    for (int w2 = 0; w2 < UPD_THREADS / 32; ++w2) t += shn[w2];
+    partial[(long long)blockIdx.x * PST] = make_double2((double)t, 0.0);
   }
-  if (want_norm) {
-    __shared__ T shn[32];
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) shn[warp] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      T t = 0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += shn[w2];
-      partial[(long long)blockIdx.x * (RMAX + 1)] = make_double2((double)t, 0.0);
-    }
-  }
-  // the last block: ||w|| over the grid, then (pass 0) the DGKS test, and the
-  // Givens step once no second Gram-Schmidt pass follows
   GmresDev* sm = const_cast<GmresDev*>(s);
   if (!last_block(&sm->arrive_upd)) return;
   __shared__ double nn_s;
-  if ((threadIdx.x >> 5) == 0) {
+  if (warp == 0) {
     const double nn = warp_sum_partials_cg(partial, gridDim.x, 0).x;
-    if (threadIdx.x == 0) nn_s = nn;
+    if (lane == 0) nn_s = nn;
   }
   __syncthreads();
-  const double nn = nn_s;
-  bool final_pass = true;
-  if (pass == 0) {
-    // re-orthogonalise only if the projection removed more than 1 - 1/sqrt(2) of ||w||
-    const int r = sqrt(nn) < 0.70710678118654752 * sm->wnorm0 ? 1 : 0;
-    __syncthreads();
-    if (threadIdx.x == 0) { sm->reorth = r; sm->reorths += r; }
-    final_pass = (r == 0);
+  const double nu = sqrt(nn_s);
+  if (threadIdx.x == 0) {
+    sm->nu = nu;
+    sm->Hr[(long long)j * (RMAX + 1) + j + 1] = make_double2(nu, 0.0);
+    sm->hnext = nu;
+    sm->iters += 1;
   }
-  if (final_pass) givens_step(sm, nn);
+  if (nu == 0.0) {
+    // breakdown: the Krylov space is invariant and column j is already final
+    __syncthreads();
+    givens_column(sm, j);
+    if (threadIdx.x == 0) { sm->k = j + 1; sm->done = 1; }
+    return;
+  }
+  if (threadIdx.x == 0) sm->j = j + 1;
 }
 
 // V_{j} = w / h (j already advanced) and u = V_j
 template <class C>
-__global__ void k_scale_next(C* __restrict__ V, const C* __restrict__ w, C* __restrict__ u, long long n3,
-                             const GmresDev* __restrict__ s) {
+__global__ void k_scale_next(C* __restrict__ V, long long ld, const C* __restrict__ w, C* __restrict__ u,
+                             long long n3, const GmresDev* __restrict__ s) {
   if (s->done) return;
   const int j = s->j;
   using T = typename real_of<C>::type;
   const T inv = (T)1 / (T)s->hnext;   // reciprocal in the vector precision
-  C* Vj = V + (long long)j * n3;
+  C* Vj = V + (long long)j * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     const C v = cscale(w[e], inv);
     Vj[e] = v;
@@ -411,7 +725,7 @@ __global__ void k_norm_partial(const C* __restrict__ r, long long n3, double2* _
   double nrm = 0;   // FP64 per thread: called once per cycle
   for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nrm += (double)r[e].x * r[e].x + (double)r[e].y * r[e].y;
   const double2 t = block_sum2(make_double2(nrm, 0), sh);
-  if (threadIdx.x == 0) partial[(long long)blockIdx.x * (RMAX + 1)] = t;
+  if (threadIdx.x == 0) partial[(long long)blockIdx.x * PST] = t;
 }
 
 __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict__ partial, int nparts, double tol_abs,
@@ -426,6 +740,7 @@ __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict
   s->k = 0;
   s->resest = beta;
   s->reorth = 0;
+  s->nu = 0;
   s->arrive_dot = 0;
   s->arrive_upd = 0;
   for (int i = 0; i <= restart; ++i) s->g[i] = make_double2(0, 0);
@@ -446,33 +761,61 @@ __global__ void k_cycle_v0(const C* __restrict__ r, C* __restrict__ V, C* __rest
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k)
-__global__ void k_solve_y(GmresDev* __restrict__ s) {
-  if (threadIdx.x != 0) return;
+// Back substitution R y = g on the rotated Hessenberg matrix: the upper
+// triangle is staged in shared memory (column l holds rows 0..l at offset
+// l (l + 1) / 2) by the whole block, then one warp solves from the bottom row
+// up, each row's sum split over the lanes.
+constexpr int SOLVE_THREADS = 256;
+__global__ void __launch_bounds__(SOLVE_THREADS) k_solve_y(GmresDev* __restrict__ s) {
+  extern __shared__ __align__(16) unsigned char solve_smem[];
+  double2* R = reinterpret_cast<double2*>(solve_smem);
+  __shared__ double2 ys[RMAX];
   const int k = s->k;
+  const int tri = k * (k + 1) / 2;
+  for (int e = threadIdx.x; e < tri; e += blockDim.x) {
+    // column l = the largest l with l (l + 1) / 2 <= e
+    int l = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while (l * (l + 1) / 2 > e) --l;
+    while ((l + 1) * (l + 2) / 2 <= e) ++l;
+    const int r = e - l * (l + 1) / 2;
+    R[e] = s->H[(long long)l * (RMAX + 1) + r];
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   for (int i = k - 1; i >= 0; --i) {
-    double2 t = s->g[i];
-    for (int l = i + 1; l < k; ++l) {
-      const double2 h = s->H[(long long)l * (RMAX + 1) + i];
-      const double2 y = s->y[l];
-      t.x -= h.x * y.x - h.y * y.y;
-      t.y -= h.x * y.y + h.y * y.x;
+    double2 t = make_double2(0, 0);
+    for (int l = i + 1 + lane; l < k; l += 32) {
+      const double2 h = R[l * (l + 1) / 2 + i];
+      const double2 y = ys[l];
+      t.x += h.x * y.x - h.y * y.y;
+      t.y += h.x * y.y + h.y * y.x;
     }
-    const double2 d = s->H[(long long)i * (RMAX + 1) + i];
-    const double2 id = cinv(d);
-    s->y[i] = cmul(t, id);
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+    }
+    if (lane == 0) {
+      const double2 g = s->g[i];
+      const double2 y = cmul(make_double2(g.x - t.x, g.y - t.y), cinv(R[i * (i + 1) / 2 + i]));
+      ys[i] = y;
+      s->y[i] = y;
+    }
+    __syncwarp();
   }
 }
 
 // u = sum_{i<k} y_i V_i
 template <class C>
-__global__ void k_combine(const C* __restrict__ V, C* __restrict__ u, long long n3, const GmresDev* __restrict__ s) {
+__global__ void k_combine(const C* __restrict__ V, long long ld, C* __restrict__ u, long long n3,
+                          const GmresDev* __restrict__ s) {
   __shared__ C ys[RMAX];
   const int k = s->k;
   for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = cconv<C>(s->y[i]);
   __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     C acc = czero<C>();
-    for (int i = 0; i < k; ++i) cfma(acc, ys[i], V[(long long)i * n3 + e]);
+    for (int i = 0; i < k; ++i) cfma(acc, ys[i], V[(long long)i * ld + e]);
     u[e] = acc;
   }
 }
@@ -592,10 +935,12 @@ static vie_status krylov_alloc(vie_plan_s* P, bool need64, bool need128) {
   const int R = P->opts.restart;
   K.restart = R;
   K.n3 = n3;
+  K.ld = (n3 + 31) / 32 * 32;
+  const long long ld = K.ld;
   if (!K.state.p) {
     VIE_TRY(K.state.alloc(sizeof(GmresDev)));
     VIE_CUDA(cudaMemset(K.state.p, 0, sizeof(GmresDev)));
-    VIE_TRY(K.partial.alloc(sizeof(double2) * NPART * (RMAX + 1)));
+    VIE_TRY(K.partial.alloc(sizeof(double2) * NPART * PST));
     VIE_TRY(K.scal.alloc(sizeof(double) * 8));
     VIE_TRY(K.x128.alloc(sizeof(double2) * n3));
     VIE_TRY(K.r128.alloc(sizeof(double2) * n3));
@@ -606,19 +951,19 @@ static vie_status krylov_alloc(vie_plan_s* P, bool need64, bool need128) {
     VIE_CUDA(cudaStreamCreateWithFlags(&K.cap, cudaStreamNonBlocking));
   }
   if (need64 && !K.V64.p) {
-    VIE_TRY(K.V64.alloc(sizeof(float2) * n3 * (R + 1)));
+    VIE_TRY(K.V64.alloc(sizeof(float2) * ld * (R + 1)));
     VIE_TRY(K.u64.alloc(sizeof(float2) * n3));
     VIE_TRY(K.z64.alloc(sizeof(float2) * n3));
-    VIE_TRY(K.w64.alloc(sizeof(float2) * n3));
+    VIE_TRY(K.w64.alloc(sizeof(float2) * ld));
     VIE_TRY(K.d64.alloc(sizeof(float2) * n3));
     VIE_TRY(K.rhs64.alloc(sizeof(float2) * n3));
     VIE_TRY(K.r64.alloc(sizeof(float2) * n3));
   }
   if (need128 && !K.V128.p) {
-    VIE_TRY(K.V128.alloc(sizeof(double2) * n3 * (R + 1)));
+    VIE_TRY(K.V128.alloc(sizeof(double2) * ld * (R + 1)));
     VIE_TRY(K.u128.alloc(sizeof(double2) * n3));
     VIE_TRY(K.z128.alloc(sizeof(double2) * n3));
-    VIE_TRY(K.w128.alloc(sizeof(double2) * n3));
+    VIE_TRY(K.w128.alloc(sizeof(double2) * ld));
   }
   return VIE_OK;
 }
@@ -629,7 +974,12 @@ static int step_kernels(vie_plan_s* P) {
   return K.step_launches;
 }
 
-// enqueue one Arnoldi step (u holds v_j on entry and v_{j+1} on exit)
+template <class C>
+static size_t dot_smem() {
+  return (size_t)ST_STAGES * ST_TILE + (size_t)(ST_CONS / 32) * (4 * (RMAX + 1) + 4) * sizeof(typename Acc<C>::T);
+}
+
+// enqueue one Arnoldi step (u holds u_j on entry and u_{j+1} on exit)
 template <class C>
 static vie_status enqueue_step(vie_plan_s* P) {
   Krylov& K = *P->kry;
@@ -641,17 +991,23 @@ static vie_status enqueue_step(vie_plan_s* P) {
   C* z = KB<C>::z(K);
   C* w = KB<C>::w(K);
   const long long n3 = K.n3;
+  int* err = P->dev_err.as<int>();
+  VIE_TRY(smem_optin(k_dot_partial<C>, dot_smem<C>()));
+  VIE_TRY(smem_optin(k_update<C>, ST_STAGES * ST_TILE));
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
-  // CGS2 with the DGKS test: dot (+ grid reduction of h in its last block),
-  // update (+ ||w||, DGKS test and, on the final pass, the Givens step in its
-  // last block); the second pass exits at once when not needed
-  for (int pass = 0; pass < 2; ++pass) {
-    { Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st); k_dot_partial<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
-    { Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st); k_update<C><<<NPART, RED_THREADS, 0, st>>>(V, w, n3, s, part, pass); }
-    count_launch(2);
+  // delayed CGS2: one reduction (s, z and the Hessenberg bookkeeping in its
+  // last block) and one update (q_j, w'' and ||w''|| in its last block)
+  {
+    Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st);
+    k_dot_partial<C><<<NPART, ST_THREADS, dot_smem<C>(), st>>>(V, K.ld, w, n3, s, part, err);
   }
-  { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, w, u, n3, s); }
+  {
+    Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st);
+    k_update<C><<<NPART, UPD_THREADS, ST_STAGES * ST_TILE, st>>>(V, K.ld, w, n3, s, part, err);
+  }
+  count_launch(2);
+  { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, K.ld, w, u, n3, s); }
   count_launch(1);
   VIE_CHECK_LAUNCH();
   return VIE_OK;
@@ -721,7 +1077,8 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     }
     // run steps in chunks, polling the stop flag
     int done = 0, steps_cycle = 0;
-    const int cyc = std::min(K.restart, max_iter - total);
+    // restart columns take restart + 1 steps: the last reduction finalises the last column
+    const int cyc = std::min(K.restart, max_iter - total) + 1;
     while (!done && steps_cycle < cyc) {
       const int chunk = std::min(4, cyc - steps_cycle);
       if (prof_enabled()) {
@@ -739,8 +1096,12 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     int hk = 0;
     VIE_CUDA(cudaMemcpyAsync(&hk, &s->k, sizeof(int), cudaMemcpyDeviceToHost, st));
     // x += P^-1 (V y)
-    k_solve_y<<<1, 32, 0, st>>>(s);
-    k_combine<C><<<grid_for(n3), 256, 0, st>>>(V, u, n3, s);
+    {
+      const size_t smem = sizeof(double2) * (size_t)K.restart * (K.restart + 1) / 2;
+      VIE_TRY(smem_optin(k_solve_y, smem));
+      k_solve_y<<<1, SOLVE_THREADS, smem, st>>>(s);
+    }
+    k_combine<C><<<grid_for(n3), 256, 0, st>>>(V, K.ld, u, n3, s);
     count_launch(2);
     VIE_TRY(op_Pinv<C>(P, u, z));
     VIE_TRY(axpy_same<C>(x, z, n3, st));

@@ -44,12 +44,18 @@ __global__ void __launch_bounds__(256) k_mv_yz_fwd(const C* __restrict__ x, C* _
   const long long plane = (long long)d.ny * d.nx;
   const C* xb = x + (long long)b * d.nz * plane;
   const int nin = xg * d.ny * d.nz;
-  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
-    const int xl = e % xg;
-    const int r = e / xg;
-    const int y = r % d.ny, z = r / d.ny;
-    a[xl * SP + z * d.Py + y] = xb[(long long)z * plane + (long long)y * d.nx + x0 + xl];
-  }
+  batched_copy<8>(
+      nin,
+      [&](int e) {
+        const int xl = e % xg, r = e / xg;
+        const int y = r % d.ny, z = r / d.ny;
+        return xb[(long long)z * plane + (long long)y * d.nx + x0 + xl];
+      },
+      [&](int e, C v) {
+        const int xl = e % xg, r = e / xg;
+        const int y = r % d.ny, z = r / d.ny;
+        a[xl * SP + z * d.Py + y] = v;
+      });
   __syncthreads();
   // y lines (only the nz non-zero rows), then z lines (all Py columns); rows
   // z >= nz stay zero in both buffers
@@ -112,7 +118,7 @@ __device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, i
 // MAXE == 0: ping-pong passes over two copies; MAXE > 0: in place (for the
 // longest embeddings).
 template <class C, int MAXE>
-__global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024) k_mv_x(C* __restrict__ T, const C* __restrict__ spec,
+__global__ void __launch_bounds__(MAXE == 0 ? 512 : 1024) k_mv_x(C* __restrict__ T, const C* __restrict__ spec,
                                                                  MvDims d, FftPlanDev pl, int joint) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -121,10 +127,13 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024) k_mv_x(C* __restrict__
   const int L = d.L;
   const long long lstride = (long long)d.Pz * d.Py * d.nx;
   const long long loff = ((long long)kz * d.Py + ky) * d.nx;
-  for (int e = threadIdx.x; e < 3 * L; e += blockDim.x) {
-    const int b = e / L, i = e - b * L;
-    s[e] = i < d.nx ? T[b * lstride + loff + i] : czero<C>();
-  }
+  batched_copy<8>(
+      3 * L,
+      [&](int e) {
+        const int b = e / L, i = e - b * L;
+        return i < d.nx ? T[b * lstride + loff + i] : czero<C>();
+      },
+      [&](int e, C v) { s[e] = v; });
   __syncthreads();
   C* res = s;
   if constexpr (MAXE == 0) {
@@ -178,12 +187,18 @@ __global__ void __launch_bounds__(256) k_mv_yz_inv(const C* __restrict__ T, cons
   C* bb = s + (size_t)XG * SP;
   const C* Ta = T + (long long)a * d.Pz * d.Py * d.nx;
   const int nin = xg * d.Py * d.Pz;
-  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
-    const int xl = e % xg;
-    const int r = e / xg;
-    const int ky = r % d.Py, kz = r / d.Py;
-    ba[xl * SP + kz * d.Py + ky] = Ta[((long long)kz * d.Py + ky) * d.nx + x0 + xl];
-  }
+  batched_copy<8>(
+      nin,
+      [&](int e) {
+        const int xl = e % xg, r = e / xg;
+        const int ky = r % d.Py, kz = r / d.Py;
+        return Ta[((long long)kz * d.Py + ky) * d.nx + x0 + xl];
+      },
+      [&](int e, C v) {
+        const int xl = e % xg, r = e / xg;
+        const int ky = r % d.Py, kz = r / d.Py;
+        ba[xl * SP + kz * d.Py + ky] = v;
+      });
   __syncthreads();
   // z lines (all Py columns), then y lines (only the nz rows kept)
   C* r1 = fft_smem_pp(ba, bb, pz, SmemLines{xg * d.Py, d.Py, 1, SP, d.Py, 1}, +1);
@@ -191,18 +206,28 @@ __global__ void __launch_bounds__(256) k_mv_yz_inv(const C* __restrict__ T, cons
   const long long plane = (long long)d.ny * d.nx;
   const long long off_a = (long long)a * d.nz * plane;
   const int nout = xg * d.ny * d.nz;
-  for (int e = threadIdx.x; e < nout; e += blockDim.x) {
-    const int xl = e % xg;
+  struct XM { C x, m; };
+  auto voxel = [&](int e, int& xl, int& yy, int& z) {
+    xl = e % xg;
     const int r = e / xg;
-    const int yy = r % d.ny, z = r / d.ny;
-    const long long v = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
-    const C xv = x[off_a + v];
-    const C m = Mv[v];
-    const C g = r2[xl * SP + z * d.Py + yy];
-    // y = x - M (x + Gx)
-    const C t = cadd(xv, g);
-    y[off_a + v] = csub(xv, cmul(m, t));
-  }
+    yy = r % d.ny;
+    z = r / d.ny;
+    return (long long)z * plane + (long long)yy * d.nx + x0 + xl;
+  };
+  batched_copy<4>(
+      nout,
+      [&](int e) {
+        int xl, yy, z;
+        const long long v = voxel(e, xl, yy, z);
+        return XM{x[off_a + v], Mv[v]};
+      },
+      [&](int e, XM q) {
+        int xl, yy, z;
+        const long long v = voxel(e, xl, yy, z);
+        const C g = r2[xl * SP + z * d.Py + yy];
+        // y = x - M (x + Gx)
+        y[off_a + v] = csub(q.x, cmul(q.m, cadd(q.x, g)));
+      });
 }
 
 static inline int pick_xg(const MvDims& d, size_t csize) {
@@ -264,7 +289,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
       auto k = k_mv_x<C, 0>;
       VIE_TRY(set_smem(k, 2 * tile));
       Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);
-      k<<<d.Py * d.Pz, 256, 2 * tile, st>>>(T, spec, d, pl, 1);
+      k<<<d.Py * d.Pz, 512, 2 * tile, st>>>(T, spec, d, pl, 1);
     } else {
       int meB;
       int joint = 1;
