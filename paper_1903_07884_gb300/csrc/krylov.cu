@@ -45,6 +45,8 @@ struct GmresDev {
   double beta;                    // norm of the cycle's starting residual
   double tol_abs;                 // stop when |g_k| <= tol_abs
   double hnext;                   // scale of the next basis vector
+  double inv_next;                // 1 / hnext, in FP64 ...
+  float inv_next32;               // ... and rounded to FP32 (read by the scaling without FP64 work)
   double resest;                  // |g_k|
   int j;                          // current step
   int k;                          // final columns of the finished cycle
@@ -475,34 +477,43 @@ __global__ void __launch_bounds__(ST_THREADS) k_dot_partial(const C* __restrict_
     if (lane == 0) { my[4 * (RMAX + 1)] = al; my[4 * (RMAX + 1) + 1] = zr; my[4 * (RMAX + 1) + 2] = zi; }
   }
   __syncthreads();
-  // block sums over the consumer warps, widened to FP64 once per value
-  double* pb = reinterpret_cast<double*>(partial + (long long)blockIdx.x * PST);
-  for (int v = threadIdx.x; v < 4 * j + 3; v += blockDim.x) {
-    int src, dst;
-    if (v < 2 * j) { src = v; dst = v; }                                        // s
-    else if (v < 4 * j) { src = 2 * (RMAX + 1) + (v - 2 * j); dst = src; }     // z
-    else { src = 4 * (RMAX + 1) + (v - 4 * j); dst = v == 4 * j ? 2 * j : 2 * (RMAX + 1) + 2 * j + (v - 4 * j - 1); }
-    T t = 0;
-    for (int w2 = 0; w2 < ST_CONS / 32; ++w2) t += wsum[(size_t)w2 * ROW + src];
-    pb[dst] = (double)t;
-    if (v == 4 * j) pb[2 * j + 1] = 0.0;
+  // block sums over the consumer warps.  Partials and the scalar work of the
+  // last block stay in the accumulator precision (FP32 for a complex-FP32
+  // basis): FP64 issues at a small fraction of the FP32 rate on this part,
+  // and the tail runs on one SM while the others wait.  The Hessenberg
+  // matrix itself is stored in FP64.
+  C* pc = reinterpret_cast<C*>(partial);
+  C* pb = pc + (long long)blockIdx.x * PST;
+  for (int v = threadIdx.x; v < 2 * (j + 1); v += blockDim.x) {
+    // v < j: s_v; v == j: alpha; v = j + 1 + i: z_i; v = 2 j + 1: zeta
+    int sr, si, dst;
+    if (v < j) { sr = 2 * v; si = sr + 1; dst = v; }
+    else if (v == j) { sr = 4 * (RMAX + 1); si = -1; dst = j; }
+    else if (v < 2 * j + 1) { sr = 2 * (RMAX + 1) + 2 * (v - j - 1); si = sr + 1; dst = RMAX + 1 + (v - j - 1); }
+    else { sr = 4 * (RMAX + 1) + 1; si = sr + 1; dst = RMAX + 1 + j; }
+    T re = 0, im = 0;
+    for (int w2 = 0; w2 < ST_CONS / 32; ++w2) {
+      re += wsum[(size_t)w2 * ROW + sr];
+      if (si >= 0) im += wsum[(size_t)w2 * ROW + si];
+    }
+    pb[dst] = cmake<C>(re, im);
   }
-  // the last block: coefficients, the final column j - 1 and its rotation,
-  // the stop test, and the tentative column j
+  // the last block: s, z, beta, t, the final column j - 1 and the tentative
+  // column j, the update coefficients
   GmresDev* sm = const_cast<GmresDev*>(s);
   if (!last_block(&sm->arrive_dot)) return;
-  __shared__ double2 sv[RMAX + 1], zv[RMAX + 1];
-  __shared__ double sc_beta, sc_t[2];
+  __shared__ C sv[RMAX + 1], zv[RMAX + 1];
+  __shared__ T sc_beta, sc_t[2];
   const int nw = blockDim.x >> 5;
   for (int i = warp; i <= j; i += nw) {
     // s_i and z_i together: every lane keeps all its loads in flight
-    double2 a = make_double2(0, 0), b = make_double2(0, 0);
-    double2 pa[(NPART + 31) / 32], pz[(NPART + 31) / 32];
+    C a = czero<C>(), b = czero<C>();
+    C pa[(NPART + 31) / 32], pz[(NPART + 31) / 32];
 #pragma unroll
     for (int q = 0; q < (NPART + 31) / 32; ++q) {
       const int bk = lane + 32 * q;
-      pa[q] = bk < (int)gridDim.x ? __ldcg(partial + (long long)bk * PST + i) : make_double2(0, 0);
-      pz[q] = bk < (int)gridDim.x ? __ldcg(partial + (long long)bk * PST + RMAX + 1 + i) : make_double2(0, 0);
+      pa[q] = bk < (int)gridDim.x ? __ldcg(pc + (long long)bk * PST + i) : czero<C>();
+      pz[q] = bk < (int)gridDim.x ? __ldcg(pc + (long long)bk * PST + RMAX + 1 + i) : czero<C>();
     }
 #pragma unroll
     for (int q = 0; q < (NPART + 31) / 32; ++q) { a.x += pa[q].x; a.y += pa[q].y; b.x += pz[q].x; b.y += pz[q].y; }
@@ -515,16 +526,15 @@ __global__ void __launch_bounds__(ST_THREADS) k_dot_partial(const C* __restrict_
     if (lane == 0) { sv[i] = a; zv[i] = b; }
   }
   __syncthreads();
-  // beta^2 = alpha - |s|^2 (warp 0) and s^H z (warp 1), lane-strided with a
-  // butterfly: FP64 issues slowly here, so no long single-thread chains
+  // beta^2 = alpha - |s|^2 (warp 0) and s^H z (warp 1), lane-strided with a butterfly
   if (warp == 0) {
-    double ss = 0;
+    T ss = 0;
     for (int i = lane; i < j; i += 32) ss += sv[i].x * sv[i].x + sv[i].y * sv[i].y;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     // u_j is already orthogonal to Q up to rounding, so |s|^2 << alpha
-    if (lane == 0) sc_beta = sqrt(fmax(sv[j].x - ss, 1e-12 * sv[j].x));
+    if (lane == 0) sc_beta = sqrt(fmax(sv[j].x - ss, (T)1e-12 * sv[j].x));
   } else if (warp == 1) {
-    double tr = 0, ti = 0;
+    T tr = 0, ti = 0;
     for (int i = lane; i < j; i += 32) {
       tr += sv[i].x * zv[i].x + sv[i].y * zv[i].y;
       ti += sv[i].x * zv[i].y - sv[i].y * zv[i].x;
@@ -536,47 +546,54 @@ __global__ void __launch_bounds__(ST_THREADS) k_dot_partial(const C* __restrict_
     if (lane == 0) { sc_t[0] = zv[j].x - tr; sc_t[1] = zv[j].y - ti; }
   }
   __syncthreads();
-  const double beta = sc_beta;
-  const double2 t = make_double2(sc_t[0] / beta, sc_t[1] / beta);   // t = (zeta - s^H z) / beta
+  const T beta = sc_beta;
+  const T ib = (T)1 / beta;
+  const C t = cmake<C>(sc_t[0] * ib, sc_t[1] * ib);   // t = (zeta - s^H z) / beta
   if (j > 0) {   // column j - 1 becomes final: h_{:,j-1} += nu s, h_{j,j-1} = nu beta
     const double nu = sm->nu;
     double2* hp = sm->Hr + (long long)(j - 1) * (RMAX + 1);
-    for (int i = threadIdx.x; i < j; i += blockDim.x) { hp[i].x += nu * sv[i].x; hp[i].y += nu * sv[i].y; }
-    if (threadIdx.x == 0) hp[j] = make_double2(nu * beta, 0.0);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      hp[i].x += nu * (double)sv[i].x;
+      hp[i].y += nu * (double)sv[i].y;
+    }
+    if (threadIdx.x == 0) hp[j] = make_double2(nu * (double)beta, 0.0);
   }
   __syncthreads();
   // tentative column j: rows 0..j of ([z; t] - H_{0:j,0:j-1} s) / beta, one
   // warp per row, lanes over the columns
   for (int r = warp; r <= j; r += nw) {
-    double ar = 0, ai = 0;
+    T ar = 0, ai = 0;
     for (int l = max(r - 1, 0) + lane; l < j; l += 32) {   // H[r][l] = 0 for r > l + 1
-      const double2 h = sm->Hr[(long long)l * (RMAX + 1) + r];
-      ar += h.x * sv[l].x - h.y * sv[l].y;
-      ai += h.x * sv[l].y + h.y * sv[l].x;
+      const double2 hd = sm->Hr[(long long)l * (RMAX + 1) + r];
+      const T hx = (T)hd.x, hy = (T)hd.y;
+      ar += hx * sv[l].x - hy * sv[l].y;
+      ai += hx * sv[l].y + hy * sv[l].x;
     }
     for (int o = 16; o > 0; o >>= 1) {
       ar += __shfl_xor_sync(0xffffffffu, ar, o);
       ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
     if (lane == 0) {
-      const double2 zr = r < j ? zv[r] : t;
-      sm->Hr[(long long)j * (RMAX + 1) + r] = make_double2((zr.x - ar) / beta, (zr.y - ai) / beta);
+      const C zr = r < j ? zv[r] : t;
+      sm->Hr[(long long)j * (RMAX + 1) + r] = make_double2((double)((zr.x - ar) * ib), (double)((zr.y - ai) * ib));
     }
   }
   // update coefficients: s, c = z - s t / beta, cu = t / beta, 1 / beta; the
   // rotation of column j - 1 (a sequential chain) and the stop test run beside
   // the update (k_update, block 0), off this kernel's critical path
-  const double2 tb = make_double2(t.x / beta, t.y / beta);
+  const C tb = cmake<C>(t.x * ib, t.y * ib);
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    sm->cs_s[i] = sv[i];
-    sm->cs_c[i] = make_double2(zv[i].x - (sv[i].x * tb.x - sv[i].y * tb.y), zv[i].y - (sv[i].x * tb.y + sv[i].y * tb.x));
+    const C si = sv[i], zi = zv[i];
+    sm->cs_s[i] = make_double2((double)si.x, (double)si.y);
+    sm->cs_c[i] = make_double2((double)(zi.x - (si.x * tb.x - si.y * tb.y)), (double)(zi.y - (si.x * tb.y + si.y * tb.x)));
   }
   if (threadIdx.x == 0) {
-    sm->cu = tb;
-    sm->inv_beta = 1.0 / beta;
+    sm->cu = make_double2((double)tb.x, (double)tb.y);
+    sm->inv_beta = (double)ib;
     sm->reorths += (j > 0) ? 1 : 0;
   }
 }
+
 
 // Hessenberg bookkeeping of step j, run by one warp of block 0 of k_update
 // while the other warps stream: the rotation of the now final column j - 1
@@ -688,6 +705,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(C* __restrict__ V, long 
     sm->nu = nu;
     sm->Hr[(long long)j * (RMAX + 1) + j + 1] = make_double2(nu, 0.0);
     sm->hnext = nu;
+    sm->inv_next = nu > 0.0 ? 1.0 / nu : 0.0;
+    sm->inv_next32 = (float)sm->inv_next;
     sm->iters += 1;
   }
   if (nu == 0.0) {
@@ -707,7 +726,7 @@ __global__ void k_scale_next(C* __restrict__ V, long long ld, const C* __restric
   if (s->done) return;
   const int j = s->j;
   using T = typename real_of<C>::type;
-  const T inv = (T)1 / (T)s->hnext;   // reciprocal in the vector precision
+  const T inv = sizeof(T) == 4 ? (T)s->inv_next32 : (T)s->inv_next;   // reciprocal in the vector precision
   C* Vj = V + (long long)j * ld;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     const C v = cscale(w[e], inv);
