@@ -264,6 +264,11 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   d.L = embed_len(nx); d.Py = embed_len(ny); d.Pz = embed_len(nz);
   d.Lh = d.L / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
   if ((long long)d.Py * d.Pz > 4096) { set_error("vie_plan_create: cross-section too large (Py*Pz > 4096)"); return VIE_EINVAL; }
+  if (3LL * nx * ny * nz >= (1LL << 31) - 64) {
+    // the streaming kernels index a vector with 32-bit arithmetic
+    set_error("vie_plan_create: 3*nx*ny*nz = %lld unknowns, the limit is 2^31 - 64", 3LL * nx * ny * nz);
+    return VIE_EINVAL;
+  }
   if (d.L > 2 * fft_max_len<double2>()) {
     set_error("vie_plan_create: nx=%d needs an x-embedding of %d > %d points", nx, d.L, 2 * fft_max_len<double2>());
     return VIE_EINVAL;

@@ -214,6 +214,115 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Power-of-two lines of n = 32 N1 points (N1 = 8, 16, 32) in complex FP32,
+// one warp per G = 32 / N1 lines, the arithmetic in registers.  With input
+// i = l + 32 r and output o = k1 + N1 k2,
+//   X[k1 + N1 k2] = sum_l W_32^{l k2} W_n^{l k1} sum_r x[l + 32 r] W_N1^{r k1},
+// so lane l first transforms its own N1 elements, scales them by W_n^{l k1},
+// and after one transpose through shared memory lane (g, k1) transforms the
+// 32 values over l.  Both transforms are radix-2 decimation in time.
+// ---------------------------------------------------------------------------
+template <int N>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
+  return r;
+}
+
+// natural-order N-point transform (N <= 32) of v; w32[j] = W_32^j, j < 16
+template <int N>
+__device__ __forceinline__ void dft_reg(float2 (&v)[N], const float2 (&w32)[16]) {
+  float2 a[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[bitrev<N>(i)] = v[i];
+#pragma unroll
+  for (int m = 1; m < N; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2 * m) {
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const float2 x = a[k + j];
+        const float2 b = j == 0 ? a[k + j + m] : cmul(a[k + j + m], w32[j * (16 / m)]);   // W_{2m}^j
+        a[k + j] = make_float2(x.x + b.x, x.y + b.y);
+        a[k + j + m] = make_float2(x.x - b.x, x.y - b.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = a[i];
+}
+
+template <int N1>
+__global__ void __launch_bounds__(128) k_fft_warp(const float2* __restrict__ in, float2* __restrict__ out, LineDesc d,
+                                                  const float2* __restrict__ tw, int sign, float scale) {
+  constexpr int G = 32 / N1;
+  constexpr int N = 32 * N1;
+  __shared__ float2 sm[4][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int line0 = (blockIdx.x * 4 + warp) * G;
+  if (line0 >= d.nlines) return;   // whole warps only; no block barrier below
+  float2 w32[16];   // W_32^j with the transform's sign
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    w32[j] = tw[j * (N / 32)];
+    if (sign > 0) w32[j].y = -w32[j].y;
+  }
+  float2 v[G][N1];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int line = line0 + g;
+    const bool ok = line < d.nlines;
+    const long long off = ok ? line_in_off(d, line) : 0;
+#pragma unroll
+    for (int r = 0; r < N1; ++r) {
+      const int i = lane + 32 * r;
+      v[g][r] = (ok && i < d.n_in) ? in[off + i] : make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    dft_reg<N1>(v[g], w32);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) {   // W_n^{l k1}
+      float2 t = tw[lane * k1];
+      if (sign > 0) t.y = -t.y;
+      v[g][k1] = cmul(v[g][k1], t);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) sm[warp][g * N1 + k1][lane] = v[g][k1];
+  }
+  __syncwarp();
+  float2 z[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) z[l] = sm[warp][lane][l];
+  dft_reg<32>(z, w32);
+  const int g = lane / N1, k1 = lane - g * N1;
+  const int line = line0 + g;
+  if (line < d.nlines) {
+    const long long off = line_out_off(d, line);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      const int o = k1 + N1 * k2;
+      if (o < d.n_out) out[off + o] = make_float2(z[k2].x * scale, z[k2].y * scale);
+    }
+  }
+}
+
+static vie_status launch_warp_fft(const float2* in, float2* out, const LineDesc& d, const FftPlanDev& p, int sign,
+                                  double scale, cudaStream_t st) {
+  const int N1 = p.n / 32, G = 32 / N1;
+  const int grid = (d.nlines + 4 * G - 1) / (4 * G);
+  Prof pf_("fft_warp_c64", st);
+  const float2* tw = (const float2*)p.tw;
+  if (N1 == 32) k_fft_warp<32><<<grid, 128, 0, st>>>(in, out, d, tw, sign, (float)scale);
+  else if (N1 == 16) k_fft_warp<16><<<grid, 128, 0, st>>>(in, out, d, tw, sign, (float)scale);
+  else k_fft_warp<8><<<grid, 128, 0, st>>>(in, out, d, tw, sign, (float)scale);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
 template <class C>
 static vie_status launch_lines(const C* in, C* out, const LineDesc& d, const FftPlanDev& p, int sign,
                                const C* pre, int pre_mode, int pre_stride, int pre_off, const C* post, int post_mode,
@@ -347,6 +456,9 @@ vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, in
                      cudaStream_t st) {
   if (d.n_in > f.n || d.n_out > f.n) { set_error("fft: line desc exceeds length"); return VIE_EINVAL; }
   if (!f.bluestein) {
+    // power-of-two complex-FP32 lines of 256..1024 contiguous points: the warp-register transform
+    if (sizeof(C) == 8 && d.ies == 1 && d.oes == 1 && (f.n == 256 || f.n == 512 || f.n == 1024))
+      return launch_warp_fft((const float2*)in, (float2*)out, d, plan_n<float2>(f), sign, scale, st);
     return launch_len<C>(in, out, d, plan_n<C>(f), sign, nullptr, 0, nullptr, 0, scale, tmp, st);
   }
   if (!tmp) { set_error("fft: Bluestein length %d needs a scratch buffer", f.n); return VIE_EINVAL; }

@@ -21,10 +21,13 @@ constexpr int FFT_MAX_PASSES = 16;
 struct FastDiv {
   unsigned d, m;
 };
+// m = ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2, in 32-bit
+// arithmetic: a 64-bit division would run as an FP64 subroutine on the device,
+// and FP64 issues at a small fraction of the FP32 rate on this part
 __host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
   FastDiv f;
   f.d = d;
-  f.m = d <= 1 ? 0u : (unsigned)((0x100000000ull + d - 1) / d);
+  f.m = d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u;
   return f;
 }
 __device__ __forceinline__ unsigned fdiv(unsigned t, FastDiv f) { return f.m ? __umulhi(t, f.m) : t; }

@@ -305,15 +305,20 @@ struct StreamGeom {
   int nsub, sc;       // sub-chunks and elements per sub-chunk (multiple of 32)
 };
 
+// (32-bit arithmetic: vectors hold fewer than 2^31 elements, checked at plan
+// creation, and a 64-bit division would run as an FP64 subroutine)
 template <class C>
 __device__ __forceinline__ StreamGeom stream_geom(long long n3) {
-  const long long per = ((n3 + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const unsigned n = (unsigned)n3;
+  const unsigned per = ((n + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
   StreamGeom g;
-  g.c0 = min(n3, (long long)blockIdx.x * per);
-  g.c1 = min(n3, g.c0 + per);
-  const int maxe = ST_TILE / (int)sizeof(C);
-  g.nsub = (int)((g.c1 - g.c0 + maxe - 1) / maxe);
-  g.sc = g.nsub > 0 ? (int)(((g.c1 - g.c0 + g.nsub - 1) / g.nsub + 31) / 32 * 32) : 0;
+  const unsigned c0 = min(n, blockIdx.x * per), c1 = min(n, c0 + per);
+  g.c0 = c0;
+  g.c1 = c1;
+  const unsigned maxe = ST_TILE / (unsigned)sizeof(C);
+  const unsigned len = c1 - c0;
+  g.nsub = (int)((len + maxe - 1) / maxe);
+  g.sc = g.nsub > 0 ? (int)(((len + (unsigned)g.nsub - 1) / (unsigned)g.nsub + 31) / 32 * 32) : 0;
   return g;
 }
 
@@ -739,7 +744,7 @@ __global__ void k_scale_next(C* __restrict__ V, long long ld, const C* __restric
 template <class C>
 __global__ void k_norm_partial(const C* __restrict__ r, long long n3, double2* __restrict__ partial) {
   __shared__ double2 sh[32];
-  const long long chunk = (n3 + gridDim.x - 1) / gridDim.x;
+  const long long chunk = ((unsigned)n3 + gridDim.x - 1) / gridDim.x;   // 32-bit division
   const long long c0 = blockIdx.x * chunk, c1 = min(n3, c0 + chunk);
   double nrm = 0;   // FP64 per thread: called once per cycle
   for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) nrm += (double)r[e].x * r[e].x + (double)r[e].y * r[e].y;

@@ -676,8 +676,8 @@ __global__ void k_bpack(const float2* __restrict__ D, float* __restrict__ Bp, in
   const long long total = (long long)(2 * m / TC_N) * nchunks * (TC_N * TC_KC);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int q = (int)(e % (TC_N * TC_KC));
-    const long long ct = e / (TC_N * TC_KC);
-    const int nt = (int)(ct / nchunks), c = (int)(ct % nchunks);
+    const int ct = (int)(e / (TC_N * TC_KC));
+    const int nt = ct / nchunks, c = ct - nt * nchunks;
     int row, k;
     tc_slot(q, row, k);
     const int nrow = nt * TC_N + row, kg = c * TC_KC + k;
@@ -686,8 +686,8 @@ __global__ void k_bpack(const float2* __restrict__ D, float* __restrict__ Bp, in
     const float v = co == 0 ? (ci == 0 ? d.x : -d.y) : (ci == 0 ? d.y : d.x);
     float hi, lo;
     umma::split_tf32(v, hi, lo);
-    Bp[ct * TC_BCHUNK + q] = hi;
-    Bp[ct * TC_BCHUNK + TC_N * TC_KC + q] = lo;
+    Bp[(long long)ct * TC_BCHUNK + q] = hi;
+    Bp[(long long)ct * TC_BCHUNK + TC_N * TC_KC + q] = lo;
   }
 }
 
@@ -699,8 +699,8 @@ __global__ void k_apack(const float2* __restrict__ R, const int* __restrict__ di
   const long long total = (long long)((ndisc + TC_M - 1) / TC_M) * nchunks * (TC_M * TC_KC / 2);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int q = 2 * (int)(e % (TC_M * TC_KC / 2));
-    const long long ct = e / (TC_M * TC_KC / 2);
-    const int mt = (int)(ct / nchunks), c = (int)(ct % nchunks);
+    const int ct = (int)(e / (TC_M * TC_KC / 2));
+    const int mt = ct / nchunks, c = ct - mt * nchunks;
     int row, k;
     tc_slot(q, row, k);
     const int t = mt * TC_M + row;
@@ -709,8 +709,8 @@ __global__ void k_apack(const float2* __restrict__ R, const int* __restrict__ di
     float2 hi, lo;
     umma::split_tf32(v.x, hi.x, lo.x);
     umma::split_tf32(v.y, hi.y, lo.y);
-    *(float2*)(Ap + ct * TC_ACHUNK + q) = hi;
-    *(float2*)(Ap + ct * TC_ACHUNK + TC_M * TC_KC + q) = lo;
+    *(float2*)(Ap + (long long)ct * TC_ACHUNK + q) = hi;
+    *(float2*)(Ap + (long long)ct * TC_ACHUNK + TC_M * TC_KC + q) = lo;
   }
 }
 

@@ -184,6 +184,34 @@ def test_precond_mixed_tensor_core_block_product():
     assert maxerr(z, ref) <= 2e-5
 
 
+@pytest.mark.parametrize("nx", [256, 512, 1024])
+def test_precond_mixed_power_of_two_lines(nx):
+    """Power-of-two box lengths of 256..1024 take the warp-register x-transform
+    in the mixed path (Sec. 4: the x-FFT of every line of the box, then the
+    blocks, then the inverse x-FFT); ragged line counts per warp included
+    (m = 3 * 3 * 2 = 18 lines)."""
+    cuda_or_fail()
+    p = inputs.straight_guide(nx, 3, 2, 0.05, 1.55)
+    tau = 1e-3
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, p.boxes, 3, tau)
+    r = inputs.random_field((3, p.nz, p.ny, p.nx), seed=24)
+    ref = P.apply(r)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=tau, homog=3)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    vie.vie_profile_enable(1)
+    vie.vie_profile_reset()
+    z = plan.precond(to_device(r), vie.VIE_MIXED).cpu().numpy()
+    table = vie.profile_table()
+    vie.vie_profile_enable(0)
+    plan.close()
+    assert table.get("fft_warp_c64", (0, 0.0))[0] == 2, table
+    assert relerr(z, ref) <= 2e-6
+    assert maxerr(z, ref) <= 2e-5
+
+
 @pytest.mark.parametrize("precision,tol,bound", [(vie.VIE_FP64, 1e-11, 1e-7), (vie.VIE_MIXED, 1e-10, 1e-6)])
 def test_solve_small_straight_matches_dense_lu(precision, tol, bound):
     """64x8x4 bar with absorbers: GPU solution against the oracle's direct LU."""
