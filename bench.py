@@ -141,17 +141,17 @@ def algorithmic(kernel: str, p, plan_meta: dict):
     T = 3 * nx * Py * Pz
     oct_ = 6 * (L // 2 + 1) * (Py // 2 + 1) * (Pz // 2 + 1)
     c = 8
-    jbar = plan_meta.get("mean_j1", 25.5)          # mean number of basis vectors read per launch
+    jbar = plan_meta.get("mean_j", 25.0)           # mean Arnoldi step index j over the launches
     if kernel == "mv_yz_fwd_c64":
         return "hbm", c * (n3 + T)
     if kernel == "mv_x_c64":
         return "hbm", c * (2 * T + oct_)
     if kernel == "mv_yz_inv_c64":
         return "hbm", c * (T + n3 + N + n3)
-    if kernel == "arnoldi_dot_c64":
-        return "hbm", c * (jbar + 1) * n3
-    if kernel == "arnoldi_update_c64":
+    if kernel == "arnoldi_dot_c64":       # reads w, u_j and V_0..V_{j-1}
         return "hbm", c * (jbar + 2) * n3
+    if kernel == "arnoldi_update_c64":    # reads the same, writes q_j and w''
+        return "hbm", c * (jbar + 4) * n3
     if kernel == "block_gemv_c64":
         m, nh = plan_meta["m"], plan_meta["nhalf"]
         return "hbm", c * nh * m * m
@@ -166,6 +166,30 @@ def algorithmic(kernel: str, p, plan_meta: dict):
         flops = sum(8.0 * nb * (m - k0 - nb) ** 2 for k0, nb in steps)
         return "alu", nblk * flops / len(steps)
     return None
+
+
+# DRAM bytes per launch from the ncu step capture of the same kernel versions
+# (profiles/ncu_gmres_step_long_straight_1024x16x8.md, 1024x16x8 wire):
+# per basis column read for the Arnoldi kernels (120.4 MB at j = 36, 38
+# columns), per launch for the others.  Cleared whenever a kernel changes.
+TRAFFIC = {
+    "long_straight_1024x16x8": {
+        "arnoldi_dot_c64": ("per_column", 122.85e6 / 38),
+        "arnoldi_update_c64": ("per_column", 122.74e6 / 38),
+        "mv_x_c64": ("per_launch", 20.16e6),
+        "block_gemv_c64": ("per_launch", 132.54e6),
+    }
+}
+
+
+def traffic(kernel: str, wname: str, plan_meta: dict):
+    t = TRAFFIC.get(wname, {}).get(kernel)
+    if t is None:
+        return None
+    kind, v = t
+    if kind == "per_column":
+        return v * (plan_meta["mean_j"] + 2)
+    return v
 
 
 def _smooth(n):
@@ -398,7 +422,7 @@ def run_gpu(args):
         if kind == "hbm":
             ach = amount / (avg_ms * 1e-3) / 1e9
             roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / pk["hbm_gbs"], "traffic": None, "share": tot / total_prof,
+                    "frac": ach / pk["hbm_gbs"], "traffic": traffic(name, wname, meta), "share": tot / total_prof,
                     "avg_launch_ms": avg_ms, "launches": cnt, "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)"}
         elif kind == "tensor":
             # tf32 peak = measured sustained bf16 x the nominal tf32 / bf16 ratio (1.1 / 2.25);
@@ -546,14 +570,14 @@ def plan_meta(p, info):
     m = 3 * boxes[0][4] * boxes[0][5]
     nblk = info["precond_blocks"] / len(boxes)
     ndisc = info["precond_discarded"] / len(boxes)
-    # mean (j + 1) over the Arnoldi steps: every refinement step is one
-    # restart cycle of at most 50 steps
+    # mean step index j over the Arnoldi launches: every refinement step is
+    # one cycle of k columns, which takes the steps j = 0..k
     its, outer = info["iters_inner"], max(1, info["iters_outer"])
     per = its / outer
-    mean_j1 = (per + 1) / 2.0
+    mean_j = per / 2.0
     # the representative takes a slot of its own unless it is kept
     return {"m": m, "nblk": nblk, "nhalf": max(1.0, nblk - 1), "ndisc": ndisc, "nboxes": len(boxes),
-            "mean_j1": mean_j1}
+            "mean_j": mean_j}
 
 
 def run_profile_case(args):
