@@ -161,6 +161,214 @@ __global__ void __launch_bounds__(MAXE == 0 ? 512 : 1024) k_mv_x(C* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused x pass for power-of-two embeddings L = R1 R2 R3 in complex FP32, all
+// structure at compile time.  The forward transform is decimation in
+// frequency: pass 1 (radix R1, stride L/R1, twiddles W_L^{b q}), pass 2 inside
+// each of the R1 blocks (radix R2, twiddles W_{L/R1}^{b q}), pass 3 on R3
+// contiguous points, which leaves X[q1 + R1 q2 + R1 R2 q3] at position
+// q1 L/R1 + q2 R3 + q3.  The tensor product works on that digit-reversed order
+// in registers, and the inverse is the mirror image (conjugate butterflies,
+// conjugate twiddles applied before them, passes in reverse order), which
+// returns natural order: no permutation anywhere.  A thread keeps the same
+// positions of all three components, so the product needs no exchange; the
+// first pass reads the zero-padded line straight from global memory and the
+// last pass writes only the nx points kept.  Shared memory holds one copy
+// of the three lines with one pad slot per 16 points, which makes every
+// pass's accesses conflict-free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int xpad(int i) { return i + (i >> 4); }
+
+// W_16^j (DIR = -1) or its conjugate (DIR = +1), j compile-time after unrolling
+template <int DIR>
+__device__ __forceinline__ float2 w16(int j) {
+  constexpr float c = 0.923879532511286756f, s = 0.382683432365089772f, h = 0.707106781186547524f;
+  float2 w;
+  switch (j & 15) {
+    case 0: w = make_float2(1.f, 0.f); break;
+    case 1: w = make_float2(c, -s); break;
+    case 2: w = make_float2(h, -h); break;
+    case 3: w = make_float2(s, -c); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 5: w = make_float2(-s, -c); break;
+    case 6: w = make_float2(-h, -h); break;
+    case 7: w = make_float2(-c, -s); break;
+    case 8: w = make_float2(-1.f, 0.f); break;
+    case 9: w = make_float2(-c, s); break;
+    case 10: w = make_float2(-h, h); break;
+    case 11: w = make_float2(-s, c); break;
+    case 12: w = make_float2(0.f, 1.f); break;
+    case 13: w = make_float2(s, c); break;
+    case 14: w = make_float2(h, h); break;
+    default: w = make_float2(c, s); break;
+  }
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+template <int N>
+__host__ __device__ constexpr int bitrev_n(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
+  return r;
+}
+
+// natural-order N-point transform (N = 2, 4, 8, 16) with the sign of DIR
+template <int N, int DIR>
+__device__ __forceinline__ void dft_pow2(float2 (&v)[N]) {
+  float2 a[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[bitrev_n<N>(i)] = v[i];
+#pragma unroll
+  for (int m = 1; m < N; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2 * m) {
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const float2 x = a[k + j];
+        float2 b = a[k + j + m];
+        if (j != 0) b = cmul(b, w16<DIR>(j * (8 / m)));   // W_{2m}^j = W_16^{8 j / m}
+        a[k + j] = make_float2(x.x + b.x, x.y + b.y);
+        a[k + j + m] = make_float2(x.x - b.x, x.y - b.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = a[i];
+}
+
+template <int R1, int R2, int R3>
+__global__ void __launch_bounds__(R2 * R3, 4) k_mv_x16(float2* __restrict__ T, const float2* __restrict__ spec,
+                                                    MvDims d, const float2* __restrict__ twL) {
+  constexpr int L = R1 * R2 * R3, S1 = L / R1, S2 = S1 / R2, GPT = R1 / R3;
+  constexpr int LP = L + L / 16;
+  static_assert(R1 == R2 && R1 % R3 == 0 && S2 == R3, "pass structure");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);   // [3][LP]
+  const int t = threadIdx.x;
+  const int kyz = blockIdx.x;
+  const int ky = kyz % d.Py, kz = kyz / d.Py;
+  const long long lstride = (long long)d.Pz * d.Py * d.nx;
+  const long long loff = ((long long)kz * d.Py + ky) * d.nx;
+  // the passes other than the product take the components one at a time
+  // (the twiddles of a pass stay in registers for all three)
+  float2 w[R1];
+  float2 v[R1];
+  // forward pass 1: group b = t from global memory (zero beyond nx)
+#pragma unroll
+  for (int q = 1; q < R1; ++q) w[q] = twL[t * q];   // W_L^{b q}
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = t + S1 * r;
+      v[r] = i < d.nx ? T[a * lstride + loff + i] : make_float2(0.f, 0.f);
+    }
+    dft_pow2<R1, -1>(v);
+#pragma unroll
+    for (int q = 1; q < R1; ++q) v[q] = cmul(v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) sm[a * LP + xpad(t + S1 * q)] = v[q];
+  }
+  __syncthreads();
+  // forward pass 2: block q1, offset b2
+  const int b2 = t % S2, base2 = (t / S2) * S1;
+#pragma unroll
+  for (int q = 1; q < R2; ++q) w[q] = twL[b2 * q * R1];   // W_{L/R1}^{b q}
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int r = 0; r < R2; ++r) v[r] = sm[a * LP + xpad(base2 + b2 + S2 * r)];
+    dft_pow2<R2, -1>(v);
+#pragma unroll
+    for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < R2; ++q) sm[a * LP + xpad(base2 + b2 + S2 * q)] = v[q];
+  }
+  __syncthreads();
+  // pass 3, the tensor product and the inverse pass 3, on GPT groups of R3 contiguous points
+  const bool fy = ky > d.Py / 2, fz = kz > d.Pz / 2;
+  const int kyo = fy ? d.Py - ky : ky;
+  const int kzo = fz ? d.Pz - kz : kz;
+  const long long Q = (long long)d.Lh * d.Pyh * d.Pzh;
+  float syz[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float sg = 1.f;
+    if (fy) sg *= pair_parity(c, 1);
+    if (fz) sg *= pair_parity(c, 2);
+    syz[c] = sg;
+  }
+#pragma unroll
+  for (int g = 0; g < GPT; ++g) {
+    const int sb = GPT * t + g;
+    const int base3 = sb * R3;
+    float2 u[3][R3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < R3; ++r) u[a][r] = sm[a * LP + xpad(base3 + r)];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dft_pow2<R3, -1>(u[a]);
+    const int q1 = sb / R2, q2 = sb - (sb / R2) * R2;
+#pragma unroll
+    for (int q3 = 0; q3 < R3; ++q3) {
+      const int kx = q1 + R1 * q2 + R1 * R2 * q3;
+      const float2 X0 = u[0][q3], X1 = u[1][q3], X2 = u[2][q3];
+      const float2 gxx = spec_at(spec, 0, kx, kyo, kzo, syz[0], d, Q);
+      const float2 gxy = spec_at(spec, 1, kx, kyo, kzo, syz[1], d, Q);
+      const float2 gxz = spec_at(spec, 2, kx, kyo, kzo, syz[2], d, Q);
+      const float2 gyy = spec_at(spec, 3, kx, kyo, kzo, syz[3], d, Q);
+      const float2 gyz = spec_at(spec, 4, kx, kyo, kzo, syz[4], d, Q);
+      const float2 gzz = spec_at(spec, 5, kx, kyo, kzo, syz[5], d, Q);
+      float2 y0 = cmul(gxx, X0), y1 = cmul(gxy, X0), y2 = cmul(gxz, X0);
+      cfma(y0, gxy, X1); cfma(y1, gyy, X1); cfma(y2, gyz, X1);
+      cfma(y0, gxz, X2); cfma(y1, gyz, X2); cfma(y2, gzz, X2);
+      u[0][q3] = y0; u[1][q3] = y1; u[2][q3] = y2;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dft_pow2<R3, +1>(u[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < R3; ++r) sm[a * LP + xpad(base3 + r)] = u[a][r];
+  }
+  __syncthreads();
+  // inverse pass 2: conjugate twiddles, then conjugate butterflies
+#pragma unroll
+  for (int q = 1; q < R2; ++q) w[q].y = -w[q].y;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int q = 0; q < R2; ++q) v[q] = sm[a * LP + xpad(base2 + b2 + S2 * q)];
+#pragma unroll
+    for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], w[q]);
+    dft_pow2<R2, +1>(v);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) sm[a * LP + xpad(base2 + b2 + S2 * r)] = v[r];
+  }
+  __syncthreads();
+  // inverse pass 1, straight to global memory (the nx points kept)
+#pragma unroll
+  for (int q = 1; q < R1; ++q) {
+    w[q] = twL[t * q];
+    w[q].y = -w[q].y;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int q = 0; q < R1; ++q) v[q] = sm[a * LP + xpad(t + S1 * q)];
+#pragma unroll
+    for (int q = 1; q < R1; ++q) v[q] = cmul(v[q], w[q]);
+    dft_pow2<R1, +1>(v);
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = t + S1 * r;
+      if (i < d.nx) T[a * lstride + loff + i] = v[r];
+    }
+  }
+}
+
 // unfused x pass, step 2: tensor product on the full spectrum S[3][Pz][Py][L]
 template <class C>
 __global__ void k_mv_xmul(C* __restrict__ S, const C* __restrict__ spec, MvDims d) {
@@ -285,7 +493,14 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
   if (fused) {
     const size_t tile = (size_t)3 * d.L * sizeof(C);
-    if (2 * tile <= 200 * 1024) {
+    if (sizeof(C) == 8 && d.L == 2048) {
+      // compile-time radix structure 16 x 16 x 8 (complex FP32)
+      constexpr int L = 2048;
+      const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);
+      Prof pf_("mv_x_c64", st);
+      VIE_TRY(set_smem(k_mv_x16<16, 16, 8>, smem));
+      k_mv_x16<16, 16, 8><<<d.Py * d.Pz, 128, smem, st>>>((float2*)T, (const float2*)spec, d, (const float2*)pl.tw);
+    } else if (2 * tile <= 200 * 1024) {
       auto k = k_mv_x<C, 0>;
       VIE_TRY(set_smem(k, 2 * tile));
       Prof pf_(sizeof(C) == 8 ? "mv_x_c64" : "mv_x_c128", st);

@@ -52,8 +52,10 @@ def test_matvec_fp64_matches_oracle(shape, eps_bg):
         assert relerr(y, op.dense_matvec(A, x)) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4)])
+@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4), (1013, 3, 2)])
 def test_matvec_mixed_matches_oracle(shape):
+    """(1013, 3, 2): a ragged nx whose embedding is L = 2048, the compile-time
+    radix-16 x pass (zero padding and crop at a non-aligned edge)."""
     cuda_or_fail()
     nx, ny, nz = shape
     eps = inputs.random_permittivity(nz, ny, nx, seed=11)
