@@ -438,13 +438,28 @@ __global__ void __launch_bounds__(256) k_lu_update(double2* __restrict__ Aall, i
 // 5b. explicit inverse from the LU factors: solve L U X = P I for a chunk of
 //     CB columns; X written row-major in precision C.
 // ---------------------------------------------------------------------------
+// LU factors rounded to the inverse's precision (complex FP32 path)
+__global__ void k_lu_narrow(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// Columns j0..j0+cb-1 of D^{-1} = U^{-1} L^{-1} P: the pivoted identity
+// columns in shared memory, forward substitution with the unit lower L, back
+// substitution with U.  Column k of the factor is staged in shared memory one
+// step ahead (the load of step k+1 overlaps the update of step k), the
+// inverted diagonal is formed once up front, and the back substitution's
+// scaling is folded into each thread's update, so every step has one barrier.
 template <class C>
-__global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ LUall, const int* __restrict__ pivall,
+__global__ void __launch_bounds__(256) k_block_inv(const C* __restrict__ LUall, const int* __restrict__ pivall,
                                                    C* __restrict__ invall, int m, int CB) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* Y = reinterpret_cast<C*>(smem_raw);   // [m][CB]
+  C* col0 = Y + (size_t)m * CB;            // two staged columns
+  C* col1 = col0 + m;
+  C* dinv = col1 + m;                      // [m] 1 / U[k][k]
   using T = typename real_of<C>::type;
-  const double2* LU = LUall + (long long)blockIdx.x * m * m;
+  const C* LU = LUall + (long long)blockIdx.x * m * m;
   const int* piv = pivall + (long long)blockIdx.x * m;
   C* inv = invall + (long long)blockIdx.x * m * m;
   const int j0 = blockIdx.y * CB;
@@ -454,6 +469,13 @@ __global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ L
     const int i = e / CB, c = e - i * CB;
     Y[e] = (c < cb && i == j0 + c) ? cmake<C>(1, 0) : czero<C>();
   }
+  for (int k = tid; k < m; k += nt) {
+    const C u = LU[(long long)k * m + k];
+    const T q = (T)1 / (u.x * u.x + u.y * u.y);
+    dinv[k] = cmake<C>(u.x * q, -u.y * q);
+  }
+  if (m > 1)
+    for (int i = 1 + tid; i < m; i += nt) col0[i] = LU[i];   // column 0 of L
   __syncthreads();
   // P applied to the identity columns: the row swaps in order
   if (tid < cb) {
@@ -463,20 +485,16 @@ __global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ L
     }
   }
   __syncthreads();
-  // forward substitution with unit lower L: column k of L is staged in
-  // shared memory (one coalesced load per step), then every (row, column)
-  // update reads only shared memory
-  C* col = Y + (size_t)m * CB;   // [m] staged column
+  // forward substitution with unit lower L
   for (int k = 0; k < m - 1; ++k) {
-    for (int i = k + 1 + tid; i < m; i += nt) {
-      const double2 l = LU[(long long)k * m + i];
-      col[i] = cmake<C>((T)l.x, (T)l.y);
-    }
-    __syncthreads();
+    C* cur = (k & 1) ? col1 : col0;
+    C* nxt = (k & 1) ? col0 : col1;
+    if (k + 1 < m - 1)
+      for (int i = k + 2 + tid; i < m; i += nt) nxt[i] = LU[(long long)(k + 1) * m + i];
     const int cnt = (m - k - 1) * cb;
     for (int e = tid; e < cnt; e += nt) {
       const int i = k + 1 + e / cb, c = e % cb;
-      const C lc = col[i];
+      const C lc = cur[i];
       C y = Y[i * CB + c];
       const C yk = Y[k * CB + c];
       y.x -= lc.x * yk.x - lc.y * yk.y;
@@ -485,35 +503,130 @@ __global__ void __launch_bounds__(256) k_block_inv(const double2* __restrict__ L
     }
     __syncthreads();
   }
-  // back substitution with U (column k of U staged likewise)
+  // back substitution with U: row k of the result is Y[k] / U[k][k], written
+  // out directly; the rows above subtract U[i][k] times it
+  {
+    C* cur = col0;
+    for (int i = tid; i < m - 1; i += nt) cur[i] = LU[(long long)(m - 1) * m + i];
+  }
+  __syncthreads();
   for (int k = m - 1; k >= 0; --k) {
-    for (int i = tid; i <= k; i += nt) {
-      const double2 u = LU[(long long)k * m + i];
-      if (i == k) {
-        const double2 iu = cinv(u);
-        col[i] = cmake<C>((T)iu.x, (T)iu.y);
-      } else {
-        col[i] = cmake<C>((T)u.x, (T)u.y);
-      }
-    }
-    __syncthreads();
-    if (tid < cb) Y[k * CB + tid] = cmul(Y[k * CB + tid], col[k]);
-    __syncthreads();
+    const int par = (m - 1 - k) & 1;
+    C* cur = par ? col1 : col0;
+    C* nxt = par ? col0 : col1;
+    if (k > 0)
+      for (int i = tid; i < k - 1; i += nt) nxt[i] = LU[(long long)(k - 1) * m + i];
+    const C dk = dinv[k];
+    if (tid < cb) inv[(long long)k * m + j0 + tid] = cmul(Y[k * CB + tid], dk);
     const int cnt = k * cb;
     for (int e = tid; e < cnt; e += nt) {
       const int i = e / cb, c = e % cb;
-      const C uc = col[i];
+      const C uc = cur[i];
+      const C yk = cmul(Y[k * CB + c], dk);
       C y = Y[i * CB + c];
-      const C yk = Y[k * CB + c];
       y.x -= uc.x * yk.x - uc.y * yk.y;
       y.y -= uc.x * yk.y + uc.y * yk.x;
       Y[i * CB + c] = y;
     }
     __syncthreads();
   }
-  for (int e = tid; e < m * cb; e += nt) {
-    const int i = e / cb, c = e - i * cb;
-    inv[(long long)i * m + j0 + c] = Y[i * CB + c];
+}
+
+// Register-blocked variant for m <= 8 RPG (complex FP32): 256 threads = 8
+// row groups (one per warp) x 32 right-hand-side columns; thread (g, c) keeps
+// rows [g RPG, (g + 1) RPG) of column c in registers.  Per step the owner of
+// row k publishes it through shared memory (one barrier), and every thread
+// updates its own rows with the staged factor column, so the update touches
+// shared memory once per multiply-add (the factor) instead of four times.
+template <int RPG>
+__global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__ LUall, const int* __restrict__ pivall,
+                                                      float2* __restrict__ invall, int m) {
+  __shared__ float2 col[2][8 * RPG];
+  __shared__ float2 rowk[2][32];
+  __shared__ float2 dinv[8 * RPG];
+  __shared__ int pv[8 * RPG];
+  const float2* LU = LUall + (long long)blockIdx.x * m * m;
+  const int* piv = pivall + (long long)blockIdx.x * m;
+  float2* inv = invall + (long long)blockIdx.x * m * m;
+  const int j0 = blockIdx.y * 32;
+  const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
+  const int r0 = g * RPG;
+  for (int k = tid; k < m; k += 256) {
+    const float2 u = LU[(long long)k * m + k];
+    const float q = 1.f / (u.x * u.x + u.y * u.y);
+    dinv[k] = make_float2(u.x * q, -u.y * q);
+    pv[k] = piv[k];
+  }
+  __syncthreads();
+  // P e_{j0 + c}: apply the row swaps in order to the index of the unit entry
+  int one = j0 + c;
+  for (int k = 0; k < m; ++k) {
+    const int p = pv[k];
+    if (one == k) one = p;
+    else if (one == p) one = k;
+  }
+  float2 y[RPG];
+#pragma unroll
+  for (int q = 0; q < RPG; ++q) y[q] = make_float2((j0 + c < m && r0 + q == one) ? 1.f : 0.f, 0.f);
+  // forward substitution with unit lower L (column k of L staged one step ahead)
+  for (int i = 1 + tid; i < m; i += 256) col[0][i] = LU[i];
+  if (r0 <= 0 && 0 < r0 + RPG) rowk[0][c] = y[0];
+  __syncthreads();
+  for (int k = 0; k < m - 1; ++k) {
+    const int b = k & 1;
+    if (k + 1 < m - 1)
+      for (int i = k + 2 + tid; i < m; i += 256) col[b ^ 1][i] = LU[(long long)(k + 1) * m + i];
+    const float2 yk = rowk[b][c];
+    if (r0 + RPG > k + 1) {   // warp-uniform: this row group still has rows below k
+#pragma unroll
+      for (int q = 0; q < RPG; ++q) {
+        const int i = r0 + q;
+        if (i > k && i < m) {
+          const float2 l = col[b][i];
+          y[q].x -= l.x * yk.x - l.y * yk.y;
+          y[q].y -= l.x * yk.y + l.y * yk.x;
+        }
+      }
+    }
+    // the owner of row k + 1 publishes it for the next step
+    if (r0 <= k + 1 && k + 1 < r0 + RPG) {
+#pragma unroll
+      for (int q = 0; q < RPG; ++q)
+        if (r0 + q == k + 1) rowk[b ^ 1][c] = y[q];
+    }
+    __syncthreads();
+  }
+  // back substitution with U: row k of the result is y_k / U[k][k]
+  for (int i = tid; i < m - 1; i += 256) col[0][i] = LU[(long long)(m - 1) * m + i];
+  if (r0 <= m - 1 && m - 1 < r0 + RPG) {
+#pragma unroll
+    for (int q = 0; q < RPG; ++q)
+      if (r0 + q == m - 1) rowk[0][c] = y[q];
+  }
+  __syncthreads();
+  for (int k = m - 1; k >= 0; --k) {
+    const int b = (m - 1 - k) & 1;
+    if (k > 0)
+      for (int i = tid; i < k - 1; i += 256) col[b ^ 1][i] = LU[(long long)(k - 1) * m + i];
+    const float2 yk = cmul(rowk[b][c], dinv[k]);
+    if (g == 0 && j0 + c < m) inv[(long long)k * m + j0 + c] = yk;
+    if (r0 < k) {
+#pragma unroll
+      for (int q = 0; q < RPG; ++q) {
+        const int i = r0 + q;
+        if (i < k) {
+          const float2 u = col[b][i];
+          y[q].x -= u.x * yk.x - u.y * yk.y;
+          y[q].y -= u.x * yk.y + u.y * yk.x;
+        }
+      }
+    }
+    if (k > 0 && r0 <= k - 1 && k - 1 < r0 + RPG) {
+#pragma unroll
+      for (int q = 0; q < RPG; ++q)
+        if (r0 + q == k - 1) rowk[b ^ 1][c] = y[q];
+    }
+    __syncthreads();
   }
 }
 
@@ -932,18 +1045,36 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
       VIE_CHECK_LAUNCH();
     }
   }
-  // column chunk of the inverse: m x (CB + 1) elements of shared memory
-  auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 1)); };
+  // column chunk of the inverse: m x (CB + 3) elements of shared memory
+  auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 3)); };
   if (want64) {
     const int CB = chunk(sizeof(float2));
     dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
-    const size_t smem = sizeof(float2) * (size_t)m * (CB + 1);
-    VIE_TRY(smem_optin(k_block_inv<float2>, smem));
-    { Prof pf_("block_inv_c64", st);
-      k_block_inv<float2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB); }
-    count_launch();
-    VIE_CHECK_LAUNCH();
+    {
+      // the complex-FP32 inverse works from the factors rounded to FP32
+      DevBuf LU32;
+      VIE_TRY(LU32.alloc(sizeof(float2) * mm * B.nblk));
+      const long long tot = (long long)mm * B.nblk;
+      k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
+                                                                                          LU32.as<float2>(), tot);
+      count_launch();
+      if (m <= 8 * 48) {
+        // register-blocked: 8 row groups x 32 columns per CTA
+        dim3 gr(B.nblk, ceil_div(m, 32));
+        Prof pf_("block_inv_c64", st);
+        if (m <= 8 * 16) k_block_inv_rb<16><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
+        else if (m <= 8 * 32) k_block_inv_rb<32><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
+        else k_block_inv_rb<48><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
+      } else {
+        const size_t smem = sizeof(float2) * (size_t)m * (CB + 3);
+        VIE_TRY(smem_optin(k_block_inv<float2>, smem));
+        Prof pf_("block_inv_c64", st);
+        k_block_inv<float2><<<gi, 256, smem, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB);
+      }
+      count_launch();
+      VIE_CHECK_LAUNCH();
+    }
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
     VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
     // tensor-core operands of the representative-block product (tf32 hi/lo split)
@@ -963,7 +1094,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     const int CB = chunk(sizeof(double2));
     dim3 gi(B.nblk, ceil_div(m, CB));
     VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
-    const size_t smem = sizeof(double2) * (size_t)m * (CB + 1);
+    const size_t smem = sizeof(double2) * (size_t)m * (CB + 3);
     VIE_TRY(smem_optin(k_block_inv<double2>, smem));
     { Prof pf_("block_inv_c128", st);
       k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB); }
