@@ -369,6 +369,139 @@ __global__ void __launch_bounds__(R2 * R3, 4) k_mv_x16(float2* __restrict__ T, c
   }
 }
 
+// ---------------------------------------------------------------------------
+// yz passes for power-of-two Py, Pz (<= 32) in complex FP32: one transform per
+// thread in registers (radix-2 decimation in time), XG = 16 x-columns per CTA,
+// one shared-memory exchange between the y and the z transforms.  Shared
+// memory holds the y spectra of the nz non-zero z rows as [z][xl][ky] with a
+// pitch of Py + 1, so both the row writes and the column reads are
+// conflict-free; global accesses run along x (16 consecutive points).
+// ---------------------------------------------------------------------------
+// W_32^j (DIR = -1) or its conjugate (DIR = +1), j compile-time after unrolling
+template <int DIR>
+__device__ __forceinline__ float2 w32(int j) {
+  // cos(pi k / 16), k = 0..8
+  constexpr float Ct[9] = {1.f, 0.980785280403230449f, 0.923879532511286756f, 0.831469612302545237f,
+                           0.707106781186547524f, 0.555570233019602225f, 0.382683432365089772f,
+                           0.195090322016128268f, 0.f};
+  int k = j & 31;
+  float sg = 1.f;
+  if (k >= 16) { k -= 16; sg = -1.f; }
+  float c, s;   // cos, sin of pi k / 16
+  if (k <= 8) { c = Ct[k]; s = Ct[8 - k]; }
+  else { c = -Ct[16 - k]; s = Ct[k - 8]; }
+  c *= sg;
+  s *= sg;
+  return make_float2(c, DIR < 0 ? -s : s);
+}
+
+// natural-order N-point transform (N = 2 .. 32) with the sign of DIR
+template <int N, int DIR>
+__device__ __forceinline__ void dft_p2(float2 (&v)[N]) {
+  float2 a[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[bitrev_n<N>(i)] = v[i];
+#pragma unroll
+  for (int m = 1; m < N; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2 * m) {
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        const float2 x = a[k + j];
+        float2 b = a[k + j + m];
+        if (j != 0) b = cmul(b, w32<DIR>(j * (16 / m)));   // W_{2m}^j = W_32^{16 j / m}
+        a[k + j] = make_float2(x.x + b.x, x.y + b.y);
+        a[k + j + m] = make_float2(x.x - b.x, x.y - b.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = a[i];
+}
+
+constexpr int YZ_XG = 16;
+
+template <int PY, int PZ>
+__global__ void __launch_bounds__(128) k_mv_yz_fwd_r(const float2* __restrict__ x, float2* __restrict__ T, MvDims d) {
+  constexpr int PITCH = PY + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);   // [nz][XG][PITCH]
+  const int b = blockIdx.y, x0 = blockIdx.x * YZ_XG;
+  const int xg = min(YZ_XG, d.nx - x0);
+  const long long plane = (long long)d.ny * d.nx;
+  const float2* xb = x + (long long)b * d.nz * plane;
+  // y transforms of the rows z < nz (zero beyond ny)
+  for (int ln = threadIdx.x; ln < d.nz * YZ_XG; ln += blockDim.x) {
+    const int xl = ln % YZ_XG, z = ln / YZ_XG;
+    float2 v[PY];
+#pragma unroll
+    for (int y = 0; y < PY; ++y)
+      v[y] = (y < d.ny && xl < xg) ? xb[z * plane + (long long)y * d.nx + x0 + xl] : make_float2(0.f, 0.f);
+    dft_p2<PY, -1>(v);
+#pragma unroll
+    for (int ky = 0; ky < PY; ++ky) S[(z * YZ_XG + xl) * PITCH + ky] = v[ky];
+  }
+  __syncthreads();
+  // z transforms of the columns (xl, ky) (rows z >= nz are zero)
+  float2* Tb = T + (long long)b * PZ * PY * d.nx;
+  for (int ln = threadIdx.x; ln < YZ_XG * PY; ln += blockDim.x) {
+    const int xl = ln % YZ_XG, ky = ln / YZ_XG;
+    float2 v[PZ];
+#pragma unroll
+    for (int z = 0; z < PZ; ++z) v[z] = z < d.nz ? S[(z * YZ_XG + xl) * PITCH + ky] : make_float2(0.f, 0.f);
+    dft_p2<PZ, -1>(v);
+    if (xl < xg) {
+#pragma unroll
+      for (int kz = 0; kz < PZ; ++kz) Tb[((long long)kz * PY + ky) * d.nx + x0 + xl] = v[kz];
+    }
+  }
+}
+
+template <int PY, int PZ>
+__global__ void __launch_bounds__(128) k_mv_yz_inv_r(const float2* __restrict__ T, const float2* __restrict__ x,
+                                                     const float2* __restrict__ Mv, float2* __restrict__ y, MvDims d) {
+  constexpr int PITCH = PY + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* S = reinterpret_cast<float2*>(smem_raw);   // [nz][XG][PITCH]
+  const int a = blockIdx.y, x0 = blockIdx.x * YZ_XG;
+  const int xg = min(YZ_XG, d.nx - x0);
+  const float2* Ta = T + (long long)a * PZ * PY * d.nx;
+  // inverse z transforms of the columns (xl, ky); keep the rows z < nz
+  for (int ln = threadIdx.x; ln < YZ_XG * PY; ln += blockDim.x) {
+    const int xl = ln % YZ_XG, ky = ln / YZ_XG;
+    float2 v[PZ];
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz)
+      v[kz] = xl < xg ? Ta[((long long)kz * PY + ky) * d.nx + x0 + xl] : make_float2(0.f, 0.f);
+    dft_p2<PZ, +1>(v);
+#pragma unroll
+    for (int z = 0; z < PZ; ++z)
+      if (z < d.nz) S[(z * YZ_XG + xl) * PITCH + ky] = v[z];
+  }
+  __syncthreads();
+  // inverse y transforms of the rows z < nz, crop to ny, y = x - M (x + G x)
+  const long long plane = (long long)d.ny * d.nx;
+  const long long off_a = (long long)a * d.nz * plane;
+  for (int ln = threadIdx.x; ln < d.nz * YZ_XG; ln += blockDim.x) {
+    const int xl = ln % YZ_XG, z = ln / YZ_XG;
+    float2 v[PY];
+#pragma unroll
+    for (int ky = 0; ky < PY; ++ky) v[ky] = S[(z * YZ_XG + xl) * PITCH + ky];
+    dft_p2<PY, +1>(v);
+    if (xl < xg) {
+#pragma unroll
+      for (int yy = 0; yy < PY / 2; ++yy) {
+        if (yy < d.ny) {
+          const long long vox = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
+          const float2 xv = x[off_a + vox];
+          const float2 mv = Mv[vox];
+          y[off_a + vox] = csub(xv, cmul(mv, cadd(xv, v[yy])));
+        }
+      }
+    }
+  }
+}
+
 // unfused x pass, step 2: tensor product on the full spectrum S[3][Pz][Py][L]
 template <class C>
 __global__ void k_mv_xmul(C* __restrict__ S, const C* __restrict__ spec, MvDims d) {
@@ -481,7 +614,15 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   const size_t smemA = 2 * (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
   dim3 gA(ceil_div(d.nx, XG), 3);
   const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
-  {
+  // register transforms for the power-of-two cross-sections that have an instantiation
+  const int yzr = sizeof(C) == 8 ? ((d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0) : 0;
+  const size_t smemR = (size_t)d.nz * YZ_XG * (d.Py + 1) * sizeof(float2);
+  const dim3 gR(ceil_div(d.nx, YZ_XG), 3);
+  if (yzr) {
+    Prof pf_("mv_yz_fwd_c64", st);
+    if (yzr == 1) k_mv_yz_fwd_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
+    else k_mv_yz_fwd_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
+  } else {
     auto k = k_mv_yz_fwd<C>;
     VIE_TRY(set_smem(k, smemA));
     Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);
@@ -540,7 +681,13 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, X, st));
   }
   // pass C
-  {
+  if (yzr) {
+    Prof pf_("mv_yz_inv_c64", st);
+    if (yzr == 1)
+      k_mv_yz_inv_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)T, (const float2*)x, (const float2*)Mv, (float2*)y, d);
+    else
+      k_mv_yz_inv_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)T, (const float2*)x, (const float2*)Mv, (float2*)y, d);
+  } else {
     auto k = k_mv_yz_inv<C>;
     VIE_TRY(set_smem(k, smemA));
     Prof pf_(sizeof(C) == 8 ? "mv_yz_inv_c64" : "mv_yz_inv_c128", st);
