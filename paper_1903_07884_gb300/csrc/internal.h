@@ -70,6 +70,9 @@ struct vie_plan_s {
   std::vector<vie_box> boxes;
   cudaStream_t st = nullptr;
   int device = 0;
+  // second stream and events for the fork inside a preconditioner application
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   vie::MvDims d{};
   const vie::FftLen *fL = nullptr, *fPy = nullptr, *fPz = nullptr;

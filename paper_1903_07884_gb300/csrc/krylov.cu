@@ -89,7 +89,11 @@ void krylov_free(vie_plan_s* P) { P->kry.reset(); }
 }  // namespace vie
 
 vie_plan_s::vie_plan_s() = default;
-vie_plan_s::~vie_plan_s() = default;
+vie_plan_s::~vie_plan_s() {
+  if (side) cudaStreamDestroy(side);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+}
 
 namespace vie {
 
@@ -265,23 +269,6 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__
   return t;
 }
 
-// Sum of 16 values over a warp as a reduce-scatter butterfly (16 shuffles
-// instead of 5 per value): returns, in every lane, the warp sum of value
-// (lane >> 1) & 15.
-template <class T>
-__device__ __forceinline__ T warp_reduce16(const T (&v)[16], int lane) {
-  T a8[8], a4[4], a2[2];
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) a8[k] = (b4 ? v[8 + k] : v[k]) + __shfl_xor_sync(0xffffffffu, b4 ? v[k] : v[8 + k], 16);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) a4[k] = (b3 ? a8[4 + k] : a8[k]) + __shfl_xor_sync(0xffffffffu, b3 ? a8[k] : a8[4 + k], 8);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) a2[k] = (b2 ? a4[2 + k] : a4[k]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[k] : a4[2 + k], 4);
-  T a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
-  a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-  return a1;
-}
 
 // ---------------------------------------------------------------------------
 // Streaming Arnoldi passes.  The basis (columns of stride ld, a multiple of

@@ -1114,6 +1114,11 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
 
 vie_status precond_build(vie_plan_s* P) {
   reset_graphs(P);   // captured Arnoldi steps point at the old blocks
+  if (!P->side) {
+    VIE_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+    VIE_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    VIE_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  }
   precond_free(P);
   if (P->opts.precond == VIE_PREC_NONE) { P->prec_built = true; P->kept_fraction = 0; return VIE_OK; }
   const auto t0 = std::chrono::steady_clock::now();
@@ -1178,7 +1183,31 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
                 (long long)n, (long long)nyb * n, (long long)nyb * nzb * n, 1};
     const long long base = ((long long)B.b.z0 * P->ny + B.b.y0) * P->nx + B.b.x0;
     VIE_TRY(fft_lines<C>(r + base, rh, ld, *B.fx, -1, 1.0, BoxBufs<C>::tmp(B), st));
-    // kept blocks (S1 pairs)
+    // kept blocks (S1 pairs) on the plan stream and, for complex FP32 with a
+    // packed representative block, the discarded frequencies on the tensor
+    // cores on a second stream: the two write disjoint frequencies of zh and
+    // overlap (HBM-bound GEMV beside the tensor-core product)
+    const bool tc = B.ndisc > 0 && sizeof(C) == 8 && B.bpack.p;
+    if (tc) {
+      VIE_CUDA(cudaEventRecord(P->ev_fork, st));
+      VIE_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+      cudaStream_t s2 = P->side;
+      {
+        Prof pf_("rep_apack", s2);
+        k_apack<<<152 * 4, 256, 0, s2>>>((const float2*)rh, B.disc.as<int>(), B.ndisc, m, n, B.apack.as<float>());
+        count_launch();
+        VIE_CHECK_LAUNCH();
+      }
+      {
+        Prof pf_("rep_gemm_tc", s2);
+        VIE_TRY(smem_optin(k_rep_gemm_tc, TC_SMEM));
+        dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / TC_N);
+        k_rep_gemm_tc<<<grid, 128, TC_SMEM, s2>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(), B.ndisc,
+                                                  (float2*)zh, m, n, P->dev_err.as<int>());
+        count_launch();
+        VIE_CHECK_LAUNCH();
+      }
+    }
     if (B.nhalf > 0) {
       const size_t smem = sizeof(C) * 2 * m;
       Prof pf_(sizeof(C) == 8 ? "block_gemv_c64" : "block_gemv_c128", st);
@@ -1187,22 +1216,9 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
       count_launch();
       VIE_CHECK_LAUNCH();
     }
-    // discarded frequencies against the representative block
-    if (B.ndisc > 0 && sizeof(C) == 8 && B.bpack.p) {
-      // tensor cores (tcgen05, 3xTF32): gather + split A, then the pipelined GEMM
-      {
-        Prof pf_("rep_apack", st);
-        k_apack<<<152 * 4, 256, 0, st>>>((const float2*)rh, B.disc.as<int>(), B.ndisc, m, n, B.apack.as<float>());
-        count_launch();
-        VIE_CHECK_LAUNCH();
-      }
-      Prof pf_("rep_gemm_tc", st);
-      VIE_TRY(smem_optin(k_rep_gemm_tc, TC_SMEM));
-      dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / TC_N);
-      k_rep_gemm_tc<<<grid, 128, TC_SMEM, st>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(), B.ndisc,
-                                                (float2*)zh, m, n, P->dev_err.as<int>());
-      count_launch();
-      VIE_CHECK_LAUNCH();
+    if (tc) {
+      VIE_CUDA(cudaEventRecord(P->ev_join, P->side));
+      VIE_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
     } else if (B.ndisc > 0) {
       Prof pf_(sizeof(C) == 8 ? "rep_gemm_c64" : "rep_gemm_c128", st);
       dim3 grid(ceil_div(B.ndisc, GB_F), ceil_div(m, GB_I));
