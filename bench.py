@@ -537,7 +537,8 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
     lat = [1000.0 * (t_done[i] - t_arr[i]) for i in range(len(reqs))]
     span = max(t_done.values()) - min(t_arr.values())
     ok = sum(1 for s in status.values() if s in (vie.VIE_OK, vie.VIE_ENOCONV))
-    out = {"requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+    converged = sum(1 for s in status.values() if s == vie.VIE_OK)
+    out = {"requests": len(reqs), "ok": ok, "converged": converged, "solves_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "max_inflight": inflight, "budget_gb": budget_gb,
            "mean_iters": float(np.mean([infos[i].iters_inner for i in infos])) if infos else None,
            "max_relres": float(max(infos[i].relres for i in infos)) if infos else None}

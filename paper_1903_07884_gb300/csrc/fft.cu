@@ -143,6 +143,10 @@ vie_status fft_get(int n, const FftLen** out) {
     VIE_TRY(upload(ci, &f->hati64));
     VIE_TRY(upload(ci, &f->hati32));
   }
+  // A pageable cudaMemcpy may return before its DMA lands, and the tables are
+  // read by kernels on non-blocking streams: make them complete before the
+  // length becomes visible to any caller.
+  VIE_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
   *out = f.get();
   (*g_fft_cache)[n] = std::move(f);
   return VIE_OK;

@@ -20,7 +20,6 @@
 
 #include "internal.h"
 #include "prof.h"
-#include "umma.cuh"
 
 namespace vie {
 
@@ -271,21 +270,19 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__
 
 
 // ---------------------------------------------------------------------------
-// Streaming Arnoldi passes.  The basis (columns of stride ld, a multiple of
-// 32 elements) is read through bulk asynchronous copies into a ring of
-// ST_STAGES shared-memory tiles: one producer thread issues the copies and 16
-// consumer warps do the arithmetic, so every SM keeps up to ST_STAGES tiles
-// in flight.  Each block owns a contiguous range of the vector cut into
-// sub-chunks of at most ST_TILE bytes; per sub-chunk the tiles are w (the
-// vector being orthogonalised) then V_0 .. V_j.  Every wait is bounded; a wait
-// that runs out sets *err and the block stops consuming.
+// Arnoldi passes over the basis (columns of stride ld, a multiple of 32
+// elements).  Each block owns a contiguous range of the vector cut into
+// sub-chunks of at most SUB_BYTES; per sub-chunk a thread visits the same KPT
+// elements of w, u_j = V_j and V_0 .. V_{j-1} in that order, reading them with
+// coalesced loads, several columns at a time so that enough loads are in
+// flight.  (A variant that streamed the columns into a ring of shared-memory
+// tiles with cp.async.bulk and mbarriers gave run-to-run different results
+// when several plans shared the GPU; the direct reads are deterministic.)
 // ---------------------------------------------------------------------------
-constexpr int ST_STAGES = 8;
-constexpr int ST_TILE = 16384;                  // bytes per tile
-constexpr int ST_CONS = 512;                    // consumer threads (warps 1..16)
-constexpr int ST_THREADS = ST_CONS + 32;
-constexpr int UPD_THREADS = ST_THREADS + 32;   // k_update: + one warp for the Hessenberg bookkeeping
-constexpr unsigned long long ST_LIMIT_NS = 1000000000ull;
+constexpr int SUB_BYTES = 16384;                // bytes of one column per sub-chunk
+constexpr int ST_CONS = 512;                    // threads doing the arithmetic
+constexpr int ST_THREADS = ST_CONS;
+constexpr int UPD_THREADS = ST_CONS + 32;       // k_update: + one warp for the Hessenberg bookkeeping
 
 struct StreamGeom {
   long long c0, c1;   // the block's element range
@@ -302,69 +299,11 @@ __device__ __forceinline__ StreamGeom stream_geom(long long n3) {
   const unsigned c0 = min(n, blockIdx.x * per), c1 = min(n, c0 + per);
   g.c0 = c0;
   g.c1 = c1;
-  const unsigned maxe = ST_TILE / (unsigned)sizeof(C);
+  const unsigned maxe = SUB_BYTES / (unsigned)sizeof(C);
   const unsigned len = c1 - c0;
   g.nsub = (int)((len + maxe - 1) / maxe);
   g.sc = g.nsub > 0 ? (int)(((len + (unsigned)g.nsub - 1) / (unsigned)g.nsub + 31) / 32 * 32) : 0;
   return g;
-}
-
-struct StreamRing {
-  uint64_t full[ST_STAGES], empty[ST_STAGES];
-};
-
-__device__ __forceinline__ void ring_init(StreamRing& r) {
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < ST_STAGES; ++i) {
-      umma::mbar_init(&r.full[i], 1);
-      umma::mbar_init(&r.empty[i], ST_CONS / 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-}
-
-// Producer (thread 0): for every sub-chunk, the w tile, the V_j tile, then
-// V_0 .. V_{j-1}, in the order the consumers take them.
-template <class C>
-__device__ void stream_produce(StreamRing& r, unsigned char* tiles, const C* __restrict__ V, long long ld,
-                               const C* __restrict__ w, int j, const StreamGeom& g, int* err) {
-  int tt = 0;
-  bool ok = true;
-  for (int sb = 0; sb < g.nsub && ok; ++sb) {
-    const long long start = g.c0 + (long long)sb * g.sc;
-    const long long cnt = min((long long)g.sc, g.c1 - start);
-    const uint32_t bytes = (uint32_t)(((cnt + 31) / 32 * 32) * sizeof(C));
-    for (int q = 0; q <= j + 1; ++q, ++tt) {
-      const int st = tt % ST_STAGES;
-      if (tt >= ST_STAGES && !umma::mbar_wait_ns(&r.empty[st], ((tt / ST_STAGES) - 1) & 1, ST_LIMIT_NS)) {
-        ok = false;
-        atomicExch(err, 1);
-        break;
-      }
-      // order: w, u_j = V_j, V_0 .. V_{j-1}
-      const C* src = q == 0 ? w + start : V + (long long)(q == 1 ? j : q - 2) * ld + start;
-      umma::mbar_arrive_expect_tx(&r.full[st], bytes);
-      umma::bulk_g2s(tiles + (size_t)st * ST_TILE, src, bytes, &r.full[st]);
-    }
-  }
-  // every copy issued must land before the block may exit
-  for (int t = (tt > ST_STAGES ? tt - ST_STAGES : 0); t < tt; ++t)
-    umma::mbar_wait_ns(&r.full[t % ST_STAGES], (t / ST_STAGES) & 1, ST_LIMIT_NS);
-}
-
-// Consumer side: wait for tile tt, hand its elements to f, release it.
-template <class C, class F>
-__device__ __forceinline__ bool stream_take(StreamRing& r, const unsigned char* tiles, int tt, bool ok, F f, int* err) {
-  const int st = tt % ST_STAGES;
-  if (ok && !umma::mbar_wait_ns(&r.full[st], (tt / ST_STAGES) & 1, ST_LIMIT_NS)) {
-    ok = false;
-    if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
-  }
-  if (ok) f(reinterpret_cast<const C*>(tiles + (size_t)st * ST_TILE));
-  __syncwarp();
-  if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(&r.empty[st])) : "memory");
-  return ok;
 }
 
 // Delayed classical Gram-Schmidt with re-orthogonalisation (one global
@@ -391,83 +330,72 @@ __device__ __forceinline__ bool stream_take(StreamRing& r, const unsigned char* 
 template <class C>
 __global__ void __launch_bounds__(ST_THREADS) k_dot_partial(const C* __restrict__ V, long long ld,
                                                             const C* __restrict__ w, long long n3,
-                                                            GmresDev* __restrict__ s, double2* __restrict__ partial,
-                                                            int* __restrict__ err) {
+                                                            GmresDev* __restrict__ s, double2* __restrict__ partial) {
   using T = typename Acc<C>::T;
-  constexpr int KPT = ST_TILE / (int)sizeof(C) / ST_CONS;   // elements per consumer thread per tile
-  constexpr int ROW = 4 * (RMAX + 1) + 4;                    // per warp: s (2 per column), z (2), alpha, zeta
-  extern __shared__ __align__(128) unsigned char tiles[];
-  __shared__ StreamRing ring;
+  constexpr int KPT = SUB_BYTES / (int)sizeof(C) / ST_CONS;   // elements per thread per sub-chunk
+  constexpr int ROW = 4 * (RMAX + 1) + 4;                     // per warp: s (2 per column), z (2), alpha, zeta
+  extern __shared__ __align__(16) unsigned char dot_smem[];
+  T* wsum = reinterpret_cast<T*>(dot_smem);                   // [16][ROW]
   if (s->done) return;
   const int j = s->j;
   const StreamGeom g = stream_geom<C>(n3);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* wsum = reinterpret_cast<T*>(tiles + (size_t)ST_STAGES * ST_TILE);   // [16][ROW]
-  ring_init(ring);
-  if (warp == 0) {
-    if (lane == 0) stream_produce<C>(ring, tiles, V, ld, w, j, g, err);
-  } else {
-    const int ct = threadIdx.x - 32;
-    T* my = wsum + (size_t)(warp - 1) * ROW;
-    for (int i = lane; i < ROW; i += 32) my[i] = 0;
-    __syncwarp();
-    T al = 0, zr = 0, zi = 0;
-    bool ok = true;
-    int tt = 0;
-    for (int sb = 0; sb < g.nsub; ++sb) {
-      const long long start = g.c0 + (long long)sb * g.sc;
-      const int cnt = (int)min((long long)g.sc, g.c1 - start);
-      C xw[KPT], xu[KPT];
-      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
+  const int ct = threadIdx.x;
+  T* my = wsum + (size_t)warp * ROW;
+  for (int i = lane; i < ROW; i += 32) my[i] = 0;
+  __syncwarp();
+  T al = 0, zr = 0, zi = 0;
+  for (int sb = 0; sb < g.nsub; ++sb) {
+    const long long start = g.c0 + (long long)sb * g.sc;
+    const int cnt = (int)min((long long)g.sc, g.c1 - start);
+    const C* wv = w + start;
+    const C* uv = V + (long long)j * ld + start;
+    C xw[KPT], xu[KPT];
 #pragma unroll
-        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xw[q] = e < cnt ? t[e] : czero<C>(); }
-      }, err);
-      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
+    for (int q = 0; q < KPT; ++q) {
+      const int e = ct + q * ST_CONS;
+      xw[q] = e < cnt ? wv[e] : czero<C>();
+      xu[q] = e < cnt ? uv[e] : czero<C>();
+      al += xu[q].x * xu[q].x + xu[q].y * xu[q].y;
+      zr += xu[q].x * xw[q].x + xu[q].y * xw[q].y;
+      zi += xu[q].x * xw[q].y - xu[q].y * xw[q].x;
+    }
+    for (int i0 = 0; i0 < j; i0 += 4) {
+      T a[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) a[q] = 0;
+      const int nt = min(4, j - i0);
+      C v[4][KPT];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const C* col = V + (long long)(i0 + t) * ld + start;
 #pragma unroll
         for (int q = 0; q < KPT; ++q) {
           const int e = ct + q * ST_CONS;
-          xu[q] = e < cnt ? t[e] : czero<C>();
-          al += xu[q].x * xu[q].x + xu[q].y * xu[q].y;
-          zr += xu[q].x * xw[q].x + xu[q].y * xw[q].y;
-          zi += xu[q].x * xw[q].y - xu[q].y * xw[q].x;
+          v[t][q] = (t < nt && e < cnt) ? col[e] : czero<C>();
         }
-      }, err);
-      for (int i0 = 0; i0 < j; i0 += 4) {
-        T a[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) a[q] = 0;
-        const int nt = min(4, j - i0);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (t < nt) {
-            ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* tile) {
-#pragma unroll
-              for (int q = 0; q < KPT; ++q) {
-                const int e = ct + q * ST_CONS;
-                if (e < cnt) {
-                  const C v = tile[e];
-                  a[4 * t + 0] += v.x * xu[q].x + v.y * xu[q].y;
-                  a[4 * t + 1] += v.x * xu[q].y - v.y * xu[q].x;
-                  a[4 * t + 2] += v.x * xw[q].x + v.y * xw[q].y;
-                  a[4 * t + 3] += v.x * xw[q].y - v.y * xw[q].x;
-                }
-              }
-            }, err);
-          }
-        }
-        const T r = warp_reduce16<T>(a, lane);
-        const int q = lane >> 1, col = i0 + (q >> 2), part = q & 3;
-        if ((lane & 1) == 0 && (q >> 2) < nt) my[(part < 2 ? 0 : 2 * (RMAX + 1)) + 2 * col + (part & 1)] += r;
-        __syncwarp();
       }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < KPT; ++q) {
+          a[4 * t + 0] += v[t][q].x * xu[q].x + v[t][q].y * xu[q].y;
+          a[4 * t + 1] += v[t][q].x * xu[q].y - v[t][q].y * xu[q].x;
+          a[4 * t + 2] += v[t][q].x * xw[q].x + v[t][q].y * xw[q].y;
+          a[4 * t + 3] += v[t][q].x * xw[q].y - v[t][q].y * xw[q].x;
+        }
+      const T r = warp_reduce16<T>(a, lane);
+      const int q = lane >> 1, col = i0 + (q >> 2), part = q & 3;
+      if ((lane & 1) == 0 && (q >> 2) < nt) my[(part < 2 ? 0 : 2 * (RMAX + 1)) + 2 * col + (part & 1)] += r;
+      __syncwarp();
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      al += __shfl_xor_sync(0xffffffffu, al, o);
-      zr += __shfl_xor_sync(0xffffffffu, zr, o);
-      zi += __shfl_xor_sync(0xffffffffu, zi, o);
-    }
-    if (lane == 0) { my[4 * (RMAX + 1)] = al; my[4 * (RMAX + 1) + 1] = zr; my[4 * (RMAX + 1) + 2] = zi; }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    zr += __shfl_xor_sync(0xffffffffu, zr, o);
+    zi += __shfl_xor_sync(0xffffffffu, zi, o);
+  }
+  if (lane == 0) { my[4 * (RMAX + 1)] = al; my[4 * (RMAX + 1) + 1] = zr; my[4 * (RMAX + 1) + 2] = zi; }
   __syncthreads();
   // block sums over the consumer warps.  Partials and the scalar work of the
   // last block stay in the accumulator precision (FP32 for a complex-FP32
@@ -605,11 +533,9 @@ __device__ void hessenberg_side(GmresDev* __restrict__ s, int j) {
 template <class C>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(C* __restrict__ V, long long ld, C* __restrict__ w,
                                                        long long n3, GmresDev* __restrict__ s,
-                                                       double2* __restrict__ partial, int* __restrict__ err) {
+                                                       double2* __restrict__ partial) {
   using T = typename Acc<C>::T;
-  constexpr int KPT = ST_TILE / (int)sizeof(C) / ST_CONS;
-  extern __shared__ __align__(128) unsigned char tiles[];
-  __shared__ StreamRing ring;
+  constexpr int KPT = SUB_BYTES / (int)sizeof(C) / ST_CONS;
   __shared__ C sco[RMAX + 1], cco[RMAX + 1];
   __shared__ T shn[UPD_THREADS / 32];
   if (s->done) return;
@@ -620,44 +546,46 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(C* __restrict__ V, long 
   const R ib = (R)s->inv_beta;
   const StreamGeom g = stream_geom<C>(n3);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ring_init(ring);   // (its barrier also publishes the coefficients)
+  __syncthreads();
   T nrm = 0;
-  if (warp == 0) {
-    if (lane == 0) stream_produce<C>(ring, tiles, V, ld, w, j, g, err);
-  } else if (warp == ST_THREADS / 32) {
+  if (warp == ST_CONS / 32) {
     if (blockIdx.x == 0) hessenberg_side(const_cast<GmresDev*>(s), j);
   } else {
-    const int ct = threadIdx.x - 32;
+    const int ct = threadIdx.x;
     C* Vj = V + (long long)j * ld;
-    bool ok = true;
-    int tt = 0;
     for (int sb = 0; sb < g.nsub; ++sb) {
       const long long start = g.c0 + (long long)sb * g.sc;
       const int cnt = (int)min((long long)g.sc, g.c1 - start);
       C xw[KPT], xu[KPT], as[KPT], ac[KPT];
 #pragma unroll
-      for (int q = 0; q < KPT; ++q) { as[q] = czero<C>(); ac[q] = czero<C>(); }
-      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
+      for (int q = 0; q < KPT; ++q) {
+        const int e = ct + q * ST_CONS;
+        xw[q] = e < cnt ? w[start + e] : czero<C>();
+        xu[q] = e < cnt ? Vj[start + e] : czero<C>();
+        as[q] = czero<C>();
+        ac[q] = czero<C>();
+      }
+      for (int i0 = 0; i0 < j; i0 += 4) {
+        const int nt = min(4, j - i0);
+        C v[4][KPT];
 #pragma unroll
-        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xw[q] = e < cnt ? t[e] : czero<C>(); }
-      }, err);
-      ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* t) {
-#pragma unroll
-        for (int q = 0; q < KPT; ++q) { const int e = ct + q * ST_CONS; xu[q] = e < cnt ? t[e] : czero<C>(); }
-      }, err);
-      for (int i = 0; i < j; ++i) {
-        const C hs = sco[i], hc = cco[i];
-        ok = stream_take<C>(ring, tiles, tt++, ok, [&](const C* tile) {
+        for (int t = 0; t < 4; ++t) {
+          const C* col = V + (long long)(i0 + t) * ld + start;
 #pragma unroll
           for (int q = 0; q < KPT; ++q) {
             const int e = ct + q * ST_CONS;
-            if (e < cnt) {
-              const C v = tile[e];
-              cfma(as[q], hs, v);
-              cfma(ac[q], hc, v);
-            }
+            v[t][q] = (t < nt && e < cnt) ? col[e] : czero<C>();
           }
-        }, err);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const C hs = t < nt ? sco[i0 + t] : czero<C>(), hc = t < nt ? cco[i0 + t] : czero<C>();
+#pragma unroll
+          for (int q = 0; q < KPT; ++q) {
+            cfma(as[q], hs, v[t][q]);
+            cfma(ac[q], hc, v[t][q]);
+          }
+        }
       }
 #pragma unroll
       for (int q = 0; q < KPT; ++q) {
@@ -950,7 +878,9 @@ static vie_status krylov_alloc(vie_plan_s* P, bool need64, bool need128) {
   const long long ld = K.ld;
   if (!K.state.p) {
     VIE_TRY(K.state.alloc(sizeof(GmresDev)));
-    VIE_CUDA(cudaMemset(K.state.p, 0, sizeof(GmresDev)));
+    // stream-ordered like the allocation (a legacy-stream memset would not be
+    // ordered with the plan's non-blocking stream)
+    VIE_CUDA(cudaMemsetAsync(K.state.p, 0, sizeof(GmresDev), P->st));
     VIE_TRY(K.partial.alloc(sizeof(double2) * NPART * PST));
     VIE_TRY(K.scal.alloc(sizeof(double) * 8));
     VIE_TRY(K.x128.alloc(sizeof(double2) * n3));
@@ -987,7 +917,7 @@ static int step_kernels(vie_plan_s* P) {
 
 template <class C>
 static size_t dot_smem() {
-  return (size_t)ST_STAGES * ST_TILE + (size_t)(ST_CONS / 32) * (4 * (RMAX + 1) + 4) * sizeof(typename Acc<C>::T);
+  return (size_t)(ST_CONS / 32) * (4 * (RMAX + 1) + 4) * sizeof(typename Acc<C>::T);
 }
 
 // enqueue one Arnoldi step (u holds u_j on entry and u_{j+1} on exit)
@@ -1002,20 +932,18 @@ static vie_status enqueue_step(vie_plan_s* P) {
   C* z = KB<C>::z(K);
   C* w = KB<C>::w(K);
   const long long n3 = K.n3;
-  int* err = P->dev_err.as<int>();
   VIE_TRY(smem_optin(k_dot_partial<C>, dot_smem<C>()));
-  VIE_TRY(smem_optin(k_update<C>, ST_STAGES * ST_TILE));
   VIE_TRY(op_Pinv<C>(P, u, z));
   VIE_TRY(op_A<C>(P, z, w));
   // delayed CGS2: one reduction (s, z and the Hessenberg bookkeeping in its
   // last block) and one update (q_j, w'' and ||w''|| in its last block)
   {
     Prof pf_(sizeof(C) == 8 ? "arnoldi_dot_c64" : "arnoldi_dot_c128", st);
-    k_dot_partial<C><<<NPART, ST_THREADS, dot_smem<C>(), st>>>(V, K.ld, w, n3, s, part, err);
+    k_dot_partial<C><<<NPART, ST_THREADS, dot_smem<C>(), st>>>(V, K.ld, w, n3, s, part);
   }
   {
     Prof pf_(sizeof(C) == 8 ? "arnoldi_update_c64" : "arnoldi_update_c128", st);
-    k_update<C><<<NPART, UPD_THREADS, ST_STAGES * ST_TILE, st>>>(V, K.ld, w, n3, s, part, err);
+    k_update<C><<<NPART, UPD_THREADS, 0, st>>>(V, K.ld, w, n3, s, part);
   }
   count_launch(2);
   { Prof pf_("arnoldi_scale", st); k_scale_next<C><<<grid_for(n3), 256, 0, st>>>(V, K.ld, w, u, n3, s); }
@@ -1231,7 +1159,17 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
       VIE_CHECK_LAUNCH();
       ++outer;
       VIE_TRY(norm128(P, r, 3, &rn));
-      if (!std::isfinite(rn)) { set_error("vie_solve: refinement diverged (non-finite residual)"); return VIE_ECUDA; }
+      if (!std::isfinite(rn)) {
+        int herr = 0;
+        VIE_CUDA(cudaMemcpyAsync(&herr, P->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        if (herr) {
+          set_error("vie_solve: a bounded wait in a kernel ran out (code %d); results invalid", herr);
+          return VIE_ETIMEOUT;
+        }
+        set_error("vie_solve: refinement diverged (non-finite residual)");
+        return VIE_ECUDA;
+      }
       if (it == 0) break;
       // a step that does not reduce the FP64 residual by 10% (twice in a row)
       // means the inner solve has nothing left to give
@@ -1254,7 +1192,7 @@ vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* 
   VIE_CUDA(cudaStreamSynchronize(st));
   if (herr) {
     cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), st);
-    set_error("vie_solve: a tensor-core wait ran out (results invalid)");
+    set_error("vie_solve: a bounded wait in a kernel ran out (code %d); results invalid", herr);
     return VIE_ETIMEOUT;
   }
   const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();

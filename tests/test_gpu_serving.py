@@ -164,3 +164,51 @@ def test_server_poisoned_request_fails_alone():
         assert res[tickets[2]][0] == vie.VIE_EINVAL
     finally:
         vie.vie_server_destroy(srv)
+
+
+def test_server_concurrent_medium_requests_bitwise():
+    """Eight medium requests (1500..3250 x 16 x 8 wires and Bragg gratings, so
+    that every SM carries blocks of several plans at once) through the server
+    with all eight in flight: each result is bitwise the result of the same
+    request solved alone.  Plans share no device state, so concurrency may
+    change timing but never a single bit."""
+    cuda_or_fail()
+    probs = []
+    for i in range(8):
+        nx = 1500 + 250 * i
+        if i % 2 == 0:
+            probs.append(inputs.straight_guide(nx, 16, 8, 0.025, 1.50 + 0.01 * i, name=f"m{i}"))
+        else:
+            probs.append(inputs.bragg_grating(nx, 16, 8, 0.025, 1.50 + 0.01 * i, name=f"m{i}"))
+    alone = []
+    for p in probs:
+        plan = Plan.for_problem(p)
+        plan.set_permittivity(p.eps)
+        w, info = plan.solve(p.e_inc)
+        assert info["relres"] <= 1e-9
+        alone.append(w.cpu().numpy())
+        plan.close()
+    srv = vie.vie_server_create(64 << 30, 8)
+    bufs, tickets = [], {}
+    for i, p in enumerate(probs):
+        eps, e = np.ascontiguousarray(p.eps), np.ascontiguousarray(p.e_inc)
+        w = np.empty(p.e_inc.shape, dtype=np.complex128)
+        bufs.append((eps, e, w))
+        st, t = vie.vie_server_submit(srv, p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, _opts(p), eps.ctypes.data,
+                                      e.ctypes.data, w.ctypes.data)
+        assert st == vie.VIE_OK
+        tickets[t] = i
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < 300:
+        for t, i in tickets.items():
+            if i not in done:
+                st, info = vie.vie_server_poll(srv, t)
+                if st != vie.VIE_PENDING:
+                    done[i] = (st, info.relres)
+        time.sleep(0.01)
+    vie.vie_server_destroy(srv)
+    assert len(done) == len(probs)
+    for i in range(len(probs)):
+        assert done[i][0] == vie.VIE_OK, (i, done[i], vie.last_error())
+        np.testing.assert_array_equal(bufs[i][2], alone[i])
