@@ -174,10 +174,10 @@ def algorithmic(kernel: str, p, plan_meta: dict):
 # columns), per launch for the others.  Cleared whenever a kernel changes.
 TRAFFIC = {
     "long_straight_1024x16x8": {
-        "arnoldi_dot_c64": ("per_column", 122.85e6 / 38),
-        "arnoldi_update_c64": ("per_column", 122.74e6 / 38),
-        "mv_x_c64": ("per_launch", 20.16e6),
-        "block_gemv_c64": ("per_launch", 132.54e6),
+        "arnoldi_dot_c64": ("per_column", 122.67e6 / 38),
+        "arnoldi_update_c64": ("per_column", 123.00e6 / 38),
+        "mv_x_c64": ("per_launch", 20.23e6),
+        "block_gemv_c64": ("per_launch", 132.71e6),
     }
 }
 
