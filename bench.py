@@ -581,6 +581,68 @@ def plan_meta(p, info):
             "mean_j": mean_j}
 
 
+def run_study(args):
+    """Qualitative studies of the method on the GPU path (FP64 GMRES(50) at
+    tolerance 1e-4, as in the paper's iteration plots; no memory reduction):
+
+    bragg  - Sec. 5.2: iterations of the three homogenisation variants
+             (mode, mean, real part of the mean) against the grating length
+             (number of periods, width step 50 nm) and against the fill D/N as
+             the corrugation depth grows (100 periods);
+    length - Sec. 3 and 4: iterations of unpreconditioned GMRES against the
+             length of a Si wire in air, beside the 1-level preconditioner.
+    Prints one JSON line with the rows."""
+    import numpy as np
+
+    from paper_1903_07884_gb300 import inputs, vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+
+    def iters(p, homog=3, precond=vie.VIE_PREC_CIRCULANT):
+        plan = Plan.for_problem(p, precision=vie.VIE_FP64, tol=1e-4, reduce_tol=0.0, homog=homog,
+                                precond=precond, max_iter=20000)
+        plan.set_permittivity(to_device(p.eps))
+        t0 = time.perf_counter()
+        _, info = plan.solve(to_device(p.e_inc), allow_noconv=True)
+        secs.append(time.perf_counter() - t0)
+        plan.close()
+        return info["iters_inner"], info["relres"]
+
+    secs = []
+
+    rows = []
+    names = {1: "mode", 2: "mean", 3: "real_mean"}
+    if args.study == "bragg":
+        # grating box 20 voxels (500 nm) wide, 8 (200 nm) high, period 14 voxels
+        # (350 nm), h = 25 nm, lambda = 1.55 um, Si in SiO2, one box
+        wide, period = 20, 14
+        for nper in (10, 20, 40, 80, 160, 320):
+            p = inputs.bragg_grating(nper * period, wide, 8, 0.025, 1.55, wide=wide, narrow=wide - 2, period=period,
+                                     nboxes=1, name=f"bragg_nper{nper}")
+            for v in (1, 2, 3):
+                it, rr = iters(p, homog=v)
+                rows.append({"sweep": "length", "n_per": nper, "dW_nm": 50, "variant": names[v], "iters": it,
+                             "relres": rr})
+        for dw in (0, 2, 4, 6, 8, 10, 12):
+            p = inputs.bragg_grating(100 * period, wide, 8, 0.025, 1.55, wide=wide, narrow=wide - dw, period=period,
+                                     nboxes=1, name=f"bragg_dw{dw}")
+            x = np.arange(p.nx)
+            fill = float(np.mean(np.where((x % period) < period // 2, wide, wide - dw)) / wide)
+            for v in (1, 2, 3):
+                it, rr = iters(p, homog=v)
+                rows.append({"sweep": "depth", "n_per": 100, "dW_nm": 25 * dw, "D_over_N": fill,
+                             "variant": names[v], "iters": it, "relres": rr})
+    else:
+        for nx in (128, 256, 512, 1024, 2048):
+            p = inputs.straight_guide(nx, 16, 8, 0.025, 1.55, name=f"wire_{nx}")
+            it0, r0 = iters(p, precond=vie.VIE_PREC_NONE)
+            it1, r1 = iters(p)
+            rows.append({"nx": nx, "length_um": nx * 0.025, "unpreconditioned_iters": it0, "relres0": r0,
+                         "preconditioned_iters": it1, "relres1": r1})
+    print(json.dumps({"study": args.study, "tol": 1e-4, "precision": "fp64", "restart": 50,
+                      "solve_seconds": [round(s, 3) for s in secs], "rows": rows}))
+    return 0
+
+
 def run_profile_case(args):
     """Build and solve the workload once in mixed precision: the launch
     sequence of one bench step, without the timing, comparison and serving
@@ -613,7 +675,11 @@ def main():
     ap.add_argument("--fp64-serial-s", type=float, default=30.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
+    ap.add_argument("--study", choices=["bragg", "length"], default=None,
+                    help="qualitative iteration studies (prints one JSON line; not a bench line)")
     args = ap.parse_args()
+    if args.study:
+        return run_study(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":

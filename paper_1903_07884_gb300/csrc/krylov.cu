@@ -984,7 +984,8 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
   if (bnorm == 0.0) return VIE_OK;
   cudaGraphExec_t& gexec = KB<C>::g(K);
   int total = 0, cycles = 0;
-  double rr = 1.0, rr_prev = 2.0;
+  double rr = 1.0, rr_best = 2.0;
+  int stalls = 0;
   while (total < max_iter) {
     // cycle start from the current residual rwork
     k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rwork, n3, part);
@@ -1063,10 +1064,15 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     total += hk;
     rr = hsc[1] / bnorm;
     if (rr <= tol || hk == 0) break;
-    // restarted cycles that no longer halve the true residual have hit the
-    // rounding floor of this precision
-    if (rr > 0.5 * rr_prev) break;
-    rr_prev = rr;
+    // restarted GMRES may converge slowly, but three cycles in a row that
+    // do not improve the best residual by 1% mean stagnation (or the
+    // rounding floor of this precision): stop and report the residual
+    if (rr > 0.99 * rr_best) {
+      if (++stalls >= 3) break;
+    } else {
+      stalls = 0;
+      rr_best = rr;
+    }
   }
   *iters = total;
   *relres = rr;
