@@ -21,6 +21,10 @@ Parity status per function (see the pin tests in tests/test_oracle_*.py):
                                    optimality, eigen-decomposition)
   precond.*                       pinned (dense definition vs per-frequency,
                                    P^-1 P x = x, S1 symmetry, tau = 0)
+  precond2.* (2-level)            pinned (2-level Frobenius projection of the
+                                   dense box matrix, level-by-level Chan-Olkin
+                                   identity, dense solve, x/y parity, ny = 1
+                                   reduces to 1-level)
   homogenize.*                    pinned (hand examples)
   gmres.gmres                     pinned (dense LU solve, 1-step exactness)
 """

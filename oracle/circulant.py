@@ -58,3 +58,25 @@ def dft_matrix(n: int) -> np.ndarray:
 def eigenvalues(c: np.ndarray) -> np.ndarray:
     """lambda_f = sum_k c_k exp(-2 pi i f k / n), i.e. F c."""
     return np.fft.fft(c)
+
+
+def chan2_from_matrix(T: np.ndarray, n1: int, n2: int) -> np.ndarray:
+    """Frobenius-nearest 2-level circulant (circulant blocks in a circulant
+    block pattern) of an (n1 n2) x (n1 n2) matrix in [i1][i2] ordering, from
+    its definition: c[k1, k2] is the mean of T over every entry whose index
+    difference is (k1, k2) modulo (n1, n2)."""
+    i1, i2 = np.divmod(np.arange(n1 * n2), n2)
+    k1 = np.mod(i1[:, None] - i1[None, :], n1)
+    k2 = np.mod(i2[:, None] - i2[None, :], n2)
+    c = np.zeros((n1, n2), dtype=np.result_type(T, np.complex128))
+    for a in range(n1):
+        for b in range(n2):
+            c[a, b] = T[(k1 == a) & (k2 == b)].mean()
+    return c
+
+
+def circulant2(c: np.ndarray) -> np.ndarray:
+    """The 2-level circulant with entries c[(i1 - j1) mod n1, (i2 - j2) mod n2]."""
+    n1, n2 = c.shape
+    i1, i2 = np.divmod(np.arange(n1 * n2), n2)
+    return c[np.mod(i1[:, None] - i1[None, :], n1), np.mod(i2[:, None] - i2[None, :], n2)]

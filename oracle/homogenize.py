@@ -36,3 +36,21 @@ def homogenize(M_box: np.ndarray, variant: int) -> np.ndarray:
     if variant == REAL_MEAN:
         return mean.real.astype(np.complex128)
     raise ValueError(f"unknown homogenisation variant {variant}")
+
+
+def homogenize_plane(M_box: np.ndarray, variant: int) -> np.ndarray:
+    """M~ for the 2-level preconditioner (Sec. 4, the 2-level paragraph, and
+    Sec. 5.3.1): the second circulant level needs an operator that is
+    Toeplitz along y as well, so M~ is made invariant in x and y.  Reading:
+    the same three variants, taken over each z-plane of the box (mode over the
+    whole box; mean over the nx ny entries of a plane; real part of that
+    mean).  Returns M~ as [nz]."""
+    nz, ny, nx = M_box.shape
+    if variant == MODE:
+        return np.full(nz, mode_value(M_box), dtype=np.complex128)
+    mean = M_box.reshape(nz, ny * nx).sum(axis=1) / (nx * ny)
+    if variant == MEAN:
+        return mean.astype(np.complex128)
+    if variant == REAL_MEAN:
+        return mean.real.astype(np.complex128)
+    raise ValueError(f"unknown homogenisation variant {variant}")

@@ -26,8 +26,9 @@ box is cladding (M~_0 = 0).  If c* = 0 (a 1-2 voxel cross-section) the entry is
 diagonal and D_f[0, 0] itself is used.
 
 Partitioning (Sec. 5.3): the preconditioner is block-diagonal over the boxes,
-each block the 1-level preconditioner of its box; unknowns outside every box
-get the identity.  Boxes must not overlap.
+each block the 1-level (or, for a box given as (x0, y0, z0, nx, ny, nz, 2),
+the 2-level, ``oracle.precond2``) preconditioner of its box; unknowns outside
+every box get the identity.  Boxes must not overlap.
 """
 from __future__ import annotations
 
@@ -103,7 +104,7 @@ class BoxPreconditioner:
 
     def __init__(self, box, M_full: np.ndarray, h: float, k: float,
                  variant: int = homogenize.REAL_MEAN, tau: float = 0.0):
-        self.box = tuple(int(v) for v in box)
+        self.box = tuple(int(v) for v in box[:6])
         x0, y0, z0, nxb, nyb, nzb = self.box
         self.n = nxb
         self.m = 3 * nyb * nzb
@@ -158,8 +159,13 @@ class Preconditioner:
                  variant: int = homogenize.REAL_MEAN, tau: float = 0.0):
         boxes = list(boxes) if boxes else [(0, 0, 0, nx, ny, nz)]
         self.shape = (3, nz, ny, nx)
-        self.boxes: List[BoxPreconditioner] = [
-            BoxPreconditioner(b, M, h, k, variant, tau) for b in boxes]
+        self.boxes = []
+        for b in boxes:
+            if len(b) > 6 and int(b[6]) == 2:
+                from .precond2 import TwoLevelBoxPreconditioner
+                self.boxes.append(TwoLevelBoxPreconditioner(b, M, h, k, variant))
+            else:
+                self.boxes.append(BoxPreconditioner(b, M, h, k, variant, tau))
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         z = r.copy()                                   # identity outside the boxes
