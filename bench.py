@@ -590,21 +590,26 @@ def run_study(args):
              (number of periods, width step 50 nm) and against the fill D/N as
              the corrugation depth grows (100 periods);
     length - Sec. 3 and 4: iterations of unpreconditioned GMRES against the
-             length of a Si wire in air, beside the 1-level preconditioner.
+             length of a Si wire in air, beside the 1-level preconditioner;
+    disk   - Sec. 5.3.1: disk resonators of radius 1-5 um beside a bus, with
+             the blocked-circulant preconditioner (reduced 1-level bus box,
+             2-level disk box, modal M~) and without one (capped at 6000).
     Prints one JSON line with the rows."""
     import numpy as np
 
     from paper_1903_07884_gb300 import inputs, vie
     from paper_1903_07884_gb300.solver import Plan, to_device
 
-    def iters(p, homog=3, precond=vie.VIE_PREC_CIRCULANT):
-        plan = Plan.for_problem(p, precision=vie.VIE_FP64, tol=1e-4, reduce_tol=0.0, homog=homog,
-                                precond=precond, max_iter=20000)
+    def iters(p, homog=3, precond=vie.VIE_PREC_CIRCULANT, reduce_tol=0.0, max_iter=20000, full=False):
+        plan = Plan.for_problem(p, precision=vie.VIE_FP64, tol=1e-4, reduce_tol=reduce_tol, homog=homog,
+                                precond=precond, max_iter=max_iter)
         plan.set_permittivity(to_device(p.eps))
         t0 = time.perf_counter()
         _, info = plan.solve(to_device(p.e_inc), allow_noconv=True)
         secs.append(time.perf_counter() - t0)
         plan.close()
+        if full:
+            return info
         return info["iters_inner"], info["relres"]
 
     secs = []
@@ -631,6 +636,19 @@ def run_study(args):
                 it, rr = iters(p, homog=v)
                 rows.append({"sweep": "depth", "n_per": 100, "dW_nm": 25 * dw, "D_over_N": fill,
                              "variant": names[v], "iters": it, "relres": rr})
+    elif args.study == "disk":
+        # Sec. 5.3.1, Table disk: 20 nm voxels, 220 nm slab, 400 nm bus, 200 nm
+        # gap; reduced 1-level bus box + 2-level disk box with the modal M~
+        for r_um in (1, 2, 3, 4, 5):
+            p = inputs.disk_resonator(int(round(r_um / 0.02)), name=f"disk_r{r_um}")
+            row = {"radius_um": r_um, "grid": [p.nx, p.ny, p.nz]}
+            info = iters(p, homog=1, reduce_tol=1e-3, full=True)
+            row.update(prec_iters=info["iters_inner"], prec_relres=info["relres"],
+                       build_s=round(info["t_setup_ms"] / 1e3, 3), prec_solve_s=round(secs[-1], 3),
+                       precond_mb=round(info["precond_bytes"] / 2 ** 20, 1))
+            it0, r0 = iters(p, precond=vie.VIE_PREC_NONE, max_iter=6000)
+            row.update(noprec_iters=it0, noprec_relres=r0, noprec_solve_s=round(secs[-1], 3))
+            rows.append(row)
     else:
         for nx in (128, 256, 512, 1024, 2048):
             p = inputs.straight_guide(nx, 16, 8, 0.025, 1.55, name=f"wire_{nx}")
@@ -675,7 +693,7 @@ def main():
     ap.add_argument("--fp64-serial-s", type=float, default=30.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
-    ap.add_argument("--study", choices=["bragg", "length"], default=None,
+    ap.add_argument("--study", choices=["bragg", "length", "disk"], default=None,
                     help="qualitative iteration studies (prints one JSON line; not a bench line)")
     args = ap.parse_args()
     if args.study:

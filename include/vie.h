@@ -67,8 +67,13 @@ typedef enum { VIE_HOM_MODE = 1, VIE_HOM_MEAN = 2, VIE_HOM_REALMEAN = 3 } vie_ho
 /* Preconditioner: none (identity) or the 1-level circulant of Sec. 4. */
 typedef enum { VIE_PREC_NONE = 0, VIE_PREC_CIRCULANT = 1 } vie_precond_kind;
 
-/* Axis-aligned partition box in voxel indices (Sec. 5.3). */
-typedef struct { int x0, y0, z0, nx, ny, nz; } vie_box;
+/* Axis-aligned partition box in voxel indices (Sec. 5.3).  levels selects the
+ * circulant approximation of the box: 1 (or 0) the 1-level preconditioner of
+ * Sec. 4 (blocks of m = 3 ny nz per x-frequency, memory reduction allowed);
+ * 2 the 2-level (Chan-Olkin) preconditioner of the paragraph after the C_B^-1
+ * display (blocks of 3 nz per (x, y) frequency pair, M homogenised over each
+ * z-plane, no memory reduction; nz <= 32). */
+typedef struct { int x0, y0, z0, nx, ny, nz, levels; } vie_box;
 
 typedef struct {
   int restart;            /* GMRES restart length (default 50)                      */

@@ -274,20 +274,34 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
     return VIE_EINVAL;
   }
   for (const vie_box& b : P->boxes) {
-    const FftLen* f;
-    VIE_TRY(fft_get(b.nx, &f));
+    if (b.levels < 0 || b.levels > 2) { set_error("vie_plan_create: box levels must be 0, 1 or 2"); return VIE_EINVAL; }
     // the Chan eigenvalues are transformed in FP64; one split doubles the limit
-    const int len = f->bluestein ? f->M : f->n;
-    if (len > 2 * fft_max_len<double2>()) {
-      set_error("vie_plan_create: box length %d needs a transform of %d points (limit %d)", b.nx, len,
-                2 * fft_max_len<double2>());
+    // (x-lines for every box, y-lines too for a 2-level box)
+    for (int axis = 0; axis < (b.levels == 2 ? 2 : 1); ++axis) {
+      const int nb = axis == 0 ? b.nx : b.ny;
+      const FftLen* f;
+      VIE_TRY(fft_get(nb, &f));
+      const int len = f->bluestein ? f->M : f->n;
+      if (len > 2 * fft_max_len<double2>()) {
+        set_error("vie_plan_create: box length %d needs a transform of %d points (limit %d)", nb, len,
+                  2 * fft_max_len<double2>());
+        return VIE_EINVAL;
+      }
+      if (len > fft_max_len<double2>()) {
+        const FftLen* h;
+        VIE_TRY(fft_get(len / 2, &h));   // half length used by the split, cached before any capture
+      }
+    }
+    if (b.levels == 2) {
+      if (b.nz > 32) { set_error("vie_plan_create: 2-level box needs nz <= 32 (blocks of 3 nz rows)"); return VIE_EINVAL; }
+      if ((b.nx / 2 + 1LL) * (b.ny / 2 + 1LL) > 65535) {
+        set_error("vie_plan_create: 2-level box stores (nx/2+1)(ny/2+1) > 65535 blocks");
+        return VIE_EINVAL;
+      }
+    } else if (3 * b.ny * b.nz > 864) {
+      set_error("vie_plan_create: box cross-section too large (m = 3 ny nz > 864)");
       return VIE_EINVAL;
     }
-    if (len > fft_max_len<double2>()) {
-      const FftLen* h;
-      VIE_TRY(fft_get(len / 2, &h));   // half length used by the split, cached before any capture
-    }
-    if (3 * b.ny * b.nz > 864) { set_error("vie_plan_create: box cross-section too large (m = 3 ny nz > 864)"); return VIE_EINVAL; }
   }
   VIE_TRY(fft_get(d.L, &P->fL));
   if (d.L > fft_max_len<float2>() || d.L > fft_max_len<double2>()) {
@@ -429,6 +443,12 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
     if (o.nboxes > 0 && o.boxes) bs.assign(o.boxes, o.boxes + o.nboxes);
     else bs.push_back(vie_box{0, 0, 0, nx, ny, nz});
     for (const vie_box& b : bs) {
+      if (b.levels == 2) {
+        const double m2 = 3.0 * b.nz, nblk = (b.nx / 2 + 1.0) * (b.ny / 2 + 1.0);
+        const double lam = 6.0 * (2 * b.nz - 1) * b.ny * b.nx * 16 * 2;
+        prec += lam + nblk * m2 * m2 * (16 + (o.precision == VIE_MIXED ? 8 : 16)) + 4.0 * b.nx * b.ny * m2 * 16;
+        continue;
+      }
       const double m = 3.0 * b.ny * b.nz;
       const double half = b.nx / 2 + 1;
       const double kept = o.reduce_tol > 0 ? std::min(half, 0.3 * half + 2) : half;

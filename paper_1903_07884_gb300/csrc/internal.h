@@ -36,6 +36,7 @@ struct MvDims {
 // One partition box of the preconditioner with its factorised blocks.
 struct BoxPrec {
   vie_box b{};
+  int levels = 1;            // 1: 1-level circulant; 2: 2-level (blocks per (f_x, f_y))
   int m = 0;                 // 3 * ny * nz
   int n = 0;                 // nx of the box (circulant length)
   int nhalf = 0;             // frequencies 0..nhalf-1 carry stored blocks (S1 symmetry)
@@ -57,6 +58,10 @@ struct BoxPrec {
   DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
   DevBuf bpack, apack;       // tensor-core operands of the representative-block product (packed tf32 hi/lo)
   const FftLen* fx = nullptr;
+  // 2-level boxes: blocks of m2 = 3 nz rows for f <= n/2, g <= ny/2, slot
+  // g * nfs + f, inverses column-major in inv64 / inv128; rhat/zhat [m2][ny][n]
+  int m2 = 0, nfs = 0, ngs = 0;
+  const FftLen* fy = nullptr;
 };
 
 struct Krylov;   // krylov.cu
@@ -115,6 +120,14 @@ vie_status precond_build(vie_plan_s* P);
 template <class C>
 vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st);
 void precond_free(vie_plan_s* P);
+vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plane);
+vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
+                                DevBuf* inv128);
+
+// precond2.cu (2-level boxes)
+vie_status build_box2(vie_plan_s* P, BoxPrec& B, bool want64, bool want128);
+template <class C>
+vie_status apply_box2(vie_plan_s* P, BoxPrec& B, const C* r, C* z, C* inv, C* rh, C* zh, C* tmp, cudaStream_t st);
 
 // krylov.cu
 vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w, vie_info* info);

@@ -54,6 +54,32 @@ __global__ void k_hom_mean(const double2* __restrict__ M, double2* __restrict__ 
   Mt[t] = make_double2(sr, real_only ? 0.0 : si);
 }
 
+// Plane mean for a 2-level box (M~ invariant in x and y): one block per
+// z-plane, a fixed-order tree sum; the value is replicated over y so that
+// M~ keeps the [nz][ny] layout of the 1-level boxes.
+__global__ void __launch_bounds__(256) k_hom_plane(const double2* __restrict__ M, double2* __restrict__ Mt, BoxDims b,
+                                                   int real_only) {
+  __shared__ double sr[256], si[256];
+  const int zb = blockIdx.x;
+  double ar = 0, ai = 0;
+  const int e_n = b.n * b.ny;
+  for (int e = threadIdx.x; e < e_n; e += blockDim.x) {
+    const int x = e % b.n, yb = e / b.n;
+    const double2 v = M[((long long)(b.z0 + zb) * b.gny + (b.y0 + yb)) * b.gnx + b.x0 + x];
+    ar += v.x;
+    ai += v.y;
+  }
+  sr[threadIdx.x] = ar;
+  si[threadIdx.x] = ai;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { sr[threadIdx.x] += sr[threadIdx.x + s]; si[threadIdx.x] += si[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  const double2 mv = make_double2(sr[0] / e_n, real_only ? 0.0 : si[0] / e_n);
+  for (int yb = threadIdx.x; yb < b.ny; yb += blockDim.x) Mt[zb * b.ny + yb] = mv;
+}
+
 // Mode of all box entries: one block keeps a table of distinct values and
 // counts.  Ties go to the smallest |value|, then the smallest (re, im).
 constexpr int MODE_MAXV = 512;
@@ -941,6 +967,112 @@ void precond_free(vie_plan_s* P) {
   P->precond_discarded = 0;
 }
 
+// Homogenised M~ of a box as [nz][ny] (Sec. 5.2): mode over the box, or the
+// (real) mean along x (1-level) or over each z-plane (2-level, plane = true).
+vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plane) {
+  const BoxDims bd = dims_of(P, b);
+  cudaStream_t st = P->st;
+  VIE_TRY(Mt.alloc(sizeof(double2) * bd.ny * bd.nz));
+  DevBuf err;
+  VIE_TRY(err.alloc(sizeof(int)));
+  VIE_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  const int real_only = P->opts.homog == VIE_HOM_REALMEAN ? 1 : 0;
+  if (P->opts.homog == VIE_HOM_MODE) {
+    k_hom_mode<<<1, 1024, 0, st>>>(P->M128.as<double2>(), Mt.as<double2>(), bd, err.as<int>());
+  } else if (plane) {
+    k_hom_plane<<<bd.nz, 256, 0, st>>>(P->M128.as<double2>(), Mt.as<double2>(), bd, real_only);
+  } else {
+    const int t = bd.ny * bd.nz;
+    k_hom_mean<<<ceil_div(t, 128), 128, 0, st>>>(P->M128.as<double2>(), Mt.as<double2>(), bd, real_only);
+  }
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  int herr = 0;
+  VIE_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (herr) { set_error("mode homogenisation: more than %d distinct values in a box", MODE_MAXV); return VIE_EINVAL; }
+  return VIE_OK;
+}
+
+// FP64 LU with partial pivoting of nblk column-major m x m blocks (in place),
+// then the explicit inverses, row-major: complex FP32 from the factors
+// narrowed to FP32 (want64) and/or complex FP64 (want128).  VIE_EINVAL if a
+// block is singular.
+vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
+                                DevBuf* inv128) {
+  cudaStream_t st = P->st;
+  const size_t mm = (size_t)m * m;
+  DevBuf piv, info;
+  VIE_TRY(piv.alloc(sizeof(int) * (size_t)m * nblk));
+  VIE_TRY(info.alloc(sizeof(int)));
+  VIE_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
+  {
+    const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
+    VIE_TRY(smem_optin(k_lu_panel, smem));
+    for (int k0 = 0; k0 < m; k0 += LU_NB) {
+      const int nb = std::min(LU_NB, m - k0);
+      {
+        Prof pf_("lu_panel", st);
+        k_lu_panel<<<nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, k0, info.as<int>());
+        count_launch();
+      }
+      const int r22 = m - k0 - nb;
+      if (r22 > 0) {
+        const int nti = ceil_div(r22, LU_TILE);
+        Prof pf_("lu_update", st);
+        k_lu_update<<<dim3(nti * nti, nblk), 256, 0, st>>>(LU.as<double2>(), m, k0, nb);
+        count_launch();
+      }
+      VIE_CHECK_LAUNCH();
+    }
+  }
+  // column chunk of the inverse: m x (CB + 3) elements of shared memory
+  auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 3)); };
+  if (want64) {
+    const int CB = chunk(sizeof(float2));
+    dim3 gi(nblk, ceil_div(m, CB));
+    VIE_TRY(inv64->alloc(sizeof(float2) * mm * nblk));
+    // the complex-FP32 inverse works from the factors rounded to FP32
+    DevBuf LU32;
+    VIE_TRY(LU32.alloc(sizeof(float2) * mm * nblk));
+    const long long tot = (long long)mm * nblk;
+    k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
+                                                                                        LU32.as<float2>(), tot);
+    count_launch();
+    if (m <= 8 * 48) {
+      // register-blocked: 8 row groups x 32 columns per CTA
+      dim3 gr(nblk, ceil_div(m, 32));
+      Prof pf_("block_inv_c64", st);
+      if (m <= 8 * 16) k_block_inv_rb<16><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
+      else if (m <= 8 * 32) k_block_inv_rb<32><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
+      else k_block_inv_rb<48><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
+    } else {
+      const size_t smem = sizeof(float2) * (size_t)m * (CB + 3);
+      VIE_TRY(smem_optin(k_block_inv<float2>, smem));
+      Prof pf_("block_inv_c64", st);
+      k_block_inv<float2><<<gi, 256, smem, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m, CB);
+    }
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  }
+  if (want128) {
+    const int CB = chunk(sizeof(double2));
+    dim3 gi(nblk, ceil_div(m, CB));
+    VIE_TRY(inv128->alloc(sizeof(double2) * mm * nblk));
+    const size_t smem = sizeof(double2) * (size_t)m * (CB + 3);
+    VIE_TRY(smem_optin(k_block_inv<double2>, smem));
+    { Prof pf_("block_inv_c128", st);
+      k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), inv128->as<double2>(), m, CB); }
+    count_launch();
+    VIE_CHECK_LAUNCH();
+  }
+  int hinfo = 0;
+  VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VIE_CUDA(cudaStreamSynchronize(st));
+  if (hinfo) { set_error("preconditioner: singular block D_f"); return VIE_EINVAL; }
+  return VIE_OK;
+}
+
 static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128) {
   const BoxDims bd = dims_of(P, B.b);
   cudaStream_t st = P->st;
@@ -949,19 +1081,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   B.rep = (n + 1) / 2 - 1;
   VIE_TRY(fft_get(n, &B.fx));
   // 1. homogenise
-  VIE_TRY(B.Mt.alloc(sizeof(double2) * bd.ny * bd.nz));
-  DevBuf err;
-  VIE_TRY(err.alloc(sizeof(int) * 8));
-  VIE_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int) * 8, st));
-  if (P->opts.homog == VIE_HOM_MODE) {
-    k_hom_mode<<<1, 1024, 0, st>>>(P->M128.as<double2>(), B.Mt.as<double2>(), bd, err.as<int>());
-  } else {
-    const int t = bd.ny * bd.nz;
-    k_hom_mean<<<ceil_div(t, 128), 128, 0, st>>>(P->M128.as<double2>(), B.Mt.as<double2>(), bd,
-                                                 P->opts.homog == VIE_HOM_REALMEAN ? 1 : 0);
-  }
-  count_launch();
-  VIE_CHECK_LAUNCH();
+  VIE_TRY(box_homogenise(P, B.b, B.Mt, false));
   // 2. Chan coefficients and eigenvalues (frequency-major)
   const int ndy = 2 * bd.ny - 1, ndz = 2 * bd.nz - 1;
   const int nl = 6 * ndz * ndy;
@@ -998,23 +1118,18 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
                                B.fmap.as<int>(), B.fsgn.as<int>(), B.disc.as<int>(), B.blkf.as<int>(), cnt.as<int>());
   count_launch();
   VIE_CHECK_LAUNCH();
-  int hc[8] = {0}, herr[8] = {0};
+  int hc[8] = {0};
   VIE_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
-  VIE_CUDA(cudaMemcpyAsync(herr, err.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
   VIE_CUDA(cudaStreamSynchronize(st));
-  if (herr[0]) { set_error("mode homogenisation: more than %d distinct values in a box", MODE_MAXV); return VIE_EINVAL; }
   B.nblk = hc[0];
   B.nkept = hc[1];
   B.ndisc = hc[2];
   B.rep = hc[3];     // now the representative's slot
   B.nhalf = hc[4];   // number of kept slots (they come first)
   // 4. assemble the stored blocks (FP64, column-major)
-  DevBuf LU, piv, info;
+  DevBuf LU;
   const size_t mm = (size_t)m * m;
   VIE_TRY(LU.alloc(sizeof(double2) * mm * B.nblk));
-  VIE_TRY(piv.alloc(sizeof(int) * (size_t)m * B.nblk));
-  VIE_TRY(info.alloc(sizeof(int)));
-  VIE_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
   {
     const long long total = (long long)mm * B.nblk;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
@@ -1025,56 +1140,8 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_CHECK_LAUNCH();
   }
   // 5. FP64 LU, then the inverse(s)
-  {
-    const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
-    VIE_TRY(smem_optin(k_lu_panel, smem));
-    for (int k0 = 0; k0 < m; k0 += LU_NB) {
-      const int nb = std::min(LU_NB, m - k0);
-      {
-        Prof pf_("lu_panel", st);
-        k_lu_panel<<<B.nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, k0, info.as<int>());
-        count_launch();
-      }
-      const int r22 = m - k0 - nb;
-      if (r22 > 0) {
-        const int nti = ceil_div(r22, LU_TILE);
-        Prof pf_("lu_update", st);
-        k_lu_update<<<dim3(nti * nti, B.nblk), 256, 0, st>>>(LU.as<double2>(), m, k0, nb);
-        count_launch();
-      }
-      VIE_CHECK_LAUNCH();
-    }
-  }
-  // column chunk of the inverse: m x (CB + 3) elements of shared memory
-  auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 3)); };
+  VIE_TRY(factor_invert_blocks(P, LU, m, B.nblk, want64, &B.inv64, want128, &B.inv128));
   if (want64) {
-    const int CB = chunk(sizeof(float2));
-    dim3 gi(B.nblk, ceil_div(m, CB));
-    VIE_TRY(B.inv64.alloc(sizeof(float2) * mm * B.nblk));
-    {
-      // the complex-FP32 inverse works from the factors rounded to FP32
-      DevBuf LU32;
-      VIE_TRY(LU32.alloc(sizeof(float2) * mm * B.nblk));
-      const long long tot = (long long)mm * B.nblk;
-      k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
-                                                                                          LU32.as<float2>(), tot);
-      count_launch();
-      if (m <= 8 * 48) {
-        // register-blocked: 8 row groups x 32 columns per CTA
-        dim3 gr(B.nblk, ceil_div(m, 32));
-        Prof pf_("block_inv_c64", st);
-        if (m <= 8 * 16) k_block_inv_rb<16><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
-        else if (m <= 8 * 32) k_block_inv_rb<32><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
-        else k_block_inv_rb<48><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m);
-      } else {
-        const size_t smem = sizeof(float2) * (size_t)m * (CB + 3);
-        VIE_TRY(smem_optin(k_block_inv<float2>, smem));
-        Prof pf_("block_inv_c64", st);
-        k_block_inv<float2><<<gi, 256, smem, st>>>(LU32.as<float2>(), piv.as<int>(), B.inv64.as<float2>(), m, CB);
-      }
-      count_launch();
-      VIE_CHECK_LAUNCH();
-    }
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
     VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
     // tensor-core operands of the representative-block product (tf32 hi/lo split)
@@ -1091,24 +1158,11 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     if (ts) VIE_TRY(B.tmp64.alloc(sizeof(float2) * ts));
   }
   if (want128) {
-    const int CB = chunk(sizeof(double2));
-    dim3 gi(B.nblk, ceil_div(m, CB));
-    VIE_TRY(B.inv128.alloc(sizeof(double2) * mm * B.nblk));
-    const size_t smem = sizeof(double2) * (size_t)m * (CB + 3);
-    VIE_TRY(smem_optin(k_block_inv<double2>, smem));
-    { Prof pf_("block_inv_c128", st);
-      k_block_inv<double2><<<gi, 256, smem, st>>>(LU.as<double2>(), piv.as<int>(), B.inv128.as<double2>(), m, CB); }
-    count_launch();
-    VIE_CHECK_LAUNCH();
     VIE_TRY(B.rhat128.alloc(sizeof(double2) * (size_t)n * m));
     VIE_TRY(B.zhat128.alloc(sizeof(double2) * (size_t)n * m));
     const size_t ts = fft_scratch_elems<double2>(*B.fx, m);
     if (ts) VIE_TRY(B.tmp128.alloc(sizeof(double2) * ts));
   }
-  int hinfo = 0;
-  VIE_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-  VIE_CUDA(cudaStreamSynchronize(st));
-  if (hinfo) { set_error("preconditioner: singular block D_f"); return VIE_EINVAL; }
   return VIE_OK;
 }
 
@@ -1129,7 +1183,8 @@ vie_status precond_build(vie_plan_s* P) {
   for (const vie_box& b : P->boxes) {
     std::unique_ptr<BoxPrec> B(new BoxPrec());
     B->b = b;
-    VIE_TRY(build_box(P, *B, want64, want128));
+    if (b.levels == 2) VIE_TRY(build_box2(P, *B, want64, want128));
+    else VIE_TRY(build_box(P, *B, want64, want128));
     kept += B->nkept;
     total += B->n;
     bytes += B->inv64.bytes + B->inv128.bytes + B->bpack.bytes + B->apack.bytes;
@@ -1177,6 +1232,10 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
     const int n = B.n, m = B.m, nyb = B.b.ny, nzb = B.b.nz;
     C* rh = BoxBufs<C>::rh(B);
     C* zh = BoxBufs<C>::zh(B);
+    if (B.levels == 2) {
+      VIE_TRY(apply_box2<C>(P, B, r, z, inv, rh, zh, BoxBufs<C>::tmp(B), st));
+      continue;
+    }
     // gather + x-FFT: line p = (alpha, zb, yb) -> R[p][f] (line-major)
     LineDesc ld{n, n, m, nyb, nzb,
                 (long long)P->nx, (long long)P->ny * P->nx, N, 1,

@@ -34,7 +34,7 @@ EPS_SIO2 = 2.085      # silicon dioxide, Table 1
 N_EFF_INC = 3.48      # phase index of the synthetic incident wave (sqrt(12.11))
 SIGMA_INC = 0.15      # Gaussian half-width of the incident profile, um
 
-Box = Tuple[int, int, int, int, int, int]   # (x0, y0, z0, nx, ny, nz)
+Box = Tuple[int, ...]   # (x0, y0, z0, nx, ny, nz[, levels]); levels 2 = 2-level circulant
 
 
 @dataclasses.dataclass
@@ -171,6 +171,36 @@ def directional_coupler(nx: int, h: float, wavelength: float, ny: int = 48, nz: 
     e = incident_field(nx, ny, nz, h, wavelength, yc, zc)
     boxes = [(0, c0, 0, nx, core_w, nz), (0, c1, 0, nx, core_w, nz)]
     return Problem(name, nx, ny, nz, h, wavelength, eps_bg, eps, e, boxes, 3, "coupler")
+
+
+def disk_resonator(radius: int, h: float = 0.02, wavelength: float = 1.545, nz: int = 11,
+                   bus_w: int = 20, gap: int = 10, margin: int = 4, lead: int = 16,
+                   eps_core: float = EPS_SI, eps_bg: float = EPS_SIO2,
+                   absorber: Optional[int] = None, disk_levels: int = 2, name: str = "disk") -> Problem:
+    """Disk resonator beside a bus waveguide (Sec. 5.3.1, Fig. "disk"): a
+    straight bus core of ``bus_w`` voxels along x, a gap of ``gap`` voxels and
+    a disk of ``radius`` voxels (voxel centres inside the circle are core),
+    both filling the slab of nz voxels, in SiO2.  The bus runs ``lead`` voxels
+    past the disk at each end and carries the absorbing ramps (default
+    ``lead - 4`` slabs, applied to core voxels, so the disk stays lossless).
+    Two boxes: the bus (1-level) and the disk's bounding square (2-level by
+    default), with the modal homogenisation the paper uses for the disk."""
+    d = 2 * radius
+    nx = d + 2 * lead
+    ny = margin + bus_w + gap + d + margin
+    la = max(lead - 4, 0) if absorber is None else absorber
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    mask[:, margin:margin + bus_w, :] = True
+    y_d0 = margin + bus_w + gap
+    xc, yc = nx / 2.0, y_d0 + radius
+    xs = np.arange(nx) + 0.5
+    ys = np.arange(ny) + 0.5
+    inside = (xs[None, :] - xc) ** 2 + (ys[:, None] - yc) ** 2 <= radius * radius
+    mask[:, inside] = True
+    eps = _fill(mask, eps_core, eps_bg, absorber_ramp(nx, la))
+    e = incident_field(nx, ny, nz, h, wavelength, (margin + bus_w / 2.0) * h, nz * h / 2.0)
+    boxes = [(0, margin, 0, nx, bus_w, nz), (lead, y_d0, 0, d, d, nz, disk_levels)]
+    return Problem(name, nx, ny, nz, h, wavelength, eps_bg, eps, e, boxes, 1, "disk")
 
 
 # ----------------------------------------------------------------------------

@@ -23,7 +23,8 @@ VIE_PREC_NONE, VIE_PREC_CIRCULANT = 0, 1
 
 class vie_box(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_int), ("y0", ctypes.c_int), ("z0", ctypes.c_int),
-                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("levels", ctypes.c_int)]
 
 
 class vie_opts(ctypes.Structure):

@@ -7,6 +7,7 @@ against the largest entry, and in norm); the FP64 preconditioner apply to
 complex-FP32 paths to the single-precision rounding of an FFT chain (2e-5)
 and of the FP32 block inverse (1e-4); solutions to 1e-6 relative error.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -119,11 +120,24 @@ def _precond_case(name):
         return inputs.straight_guide(24, 24, 8, 0.025, 1.55, core_ny=16, core_nz=8, absorber=2), 0.0, 3
     if name == "coupler_boxes":
         return inputs.directional_coupler(64, 0.025, 1.55, ny=24, nz=4, core_w=8, gap=4, margin=2), 0.0, 3
+    # 2-level boxes (Sec. 4, the 2-level paragraph; Sec. 5.3.1)
+    if name == "disk_blocked_2level":
+        return inputs.disk_resonator(6, nz=3, bus_w=4, gap=2, margin=2, lead=6), 1e-3, 1
+    if name == "two_level_prime_bluestein":
+        p = inputs.straight_guide(13, 11, 2, 0.05, 1.55, core_ny=7, absorber=2)
+        return dataclasses.replace(p, boxes=[(0, 0, 0, 13, 11, 2, 2)]), 0.0, 2
+    if name == "two_level_even":
+        p = inputs.straight_guide(32, 20, 4, 0.025, 1.55, core_ny=12, absorber=3)
+        return dataclasses.replace(p, boxes=[(0, 0, 0, 32, 20, 4, 2)]), 0.0, 3
+    if name == "two_level_m96":
+        p = inputs.straight_guide(8, 6, 32, 0.025, 1.55, core_ny=4, core_nz=24, absorber=1)
+        return dataclasses.replace(p, boxes=[(0, 0, 0, 8, 6, 32, 2)]), 0.0, 2
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["straight_full", "small_reduced", "prime_nx_bluestein", "bragg_boxes_mode",
-                                  "coupler_boxes", "wide_box_m576"])
+                                  "coupler_boxes", "wide_box_m576", "disk_blocked_2level",
+                                  "two_level_prime_bluestein", "two_level_even", "two_level_m96"])
 def test_precond_fp64_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
@@ -141,7 +155,9 @@ def test_precond_fp64_matches_oracle(name):
     assert maxerr(z, ref) <= 1e-11
 
 
-@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode", "wide_box_m576"])
+@pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode", "wide_box_m576",
+                                  "disk_blocked_2level", "two_level_prime_bluestein", "two_level_even",
+                                  "two_level_m96"])
 def test_precond_mixed_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
@@ -240,6 +256,22 @@ def test_solve_tiny_cases_match_dense_lu():
             w, info = plan.solve(p.e_inc)
             plan.close()
             assert relerr(w.cpu().numpy(), ref) <= 1e-6, (p.name, prec, info)
+
+
+@pytest.mark.parametrize("precision", [vie.VIE_FP64, vie.VIE_MIXED])
+def test_solve_disk_blocked_two_level_matches_dense_lu(precision):
+    """Disk beside a bus (Sec. 5.3.1) with the blocked-circulant preconditioner:
+    1-level bus box, 2-level disk box, modal M~."""
+    cuda_or_fail()
+    p = inputs.disk_resonator(4, nz=2, bus_w=3, gap=2, margin=2, lead=5)
+    ref = osolve.dense_solve(p)
+    plan = Plan.for_problem(p, precision=precision, tol=1e-11, reduce_tol=0.0)
+    plan.set_permittivity(p.eps)
+    w, info = plan.solve(p.e_inc)
+    plan.close()
+    assert info["relres"] <= 1e-11
+    assert info["precond_blocks"] == (p.nx // 2 + 1) + (4 + 1) * (4 + 1)
+    assert relerr(w.cpu().numpy(), ref) <= 1e-6
 
 
 def test_matvec_fp64_long_line_split():
