@@ -602,7 +602,7 @@ def run_study(args):
 
     def iters(p, homog=3, precond=vie.VIE_PREC_CIRCULANT, reduce_tol=0.0, max_iter=20000, full=False):
         plan = Plan.for_problem(p, precision=vie.VIE_FP64, tol=1e-4, reduce_tol=reduce_tol, homog=homog,
-                                precond=precond, max_iter=max_iter)
+                                precond=precond, max_iter=max_iter, restart=args.study_restart)
         plan.set_permittivity(to_device(p.eps))
         t0 = time.perf_counter()
         _, info = plan.solve(to_device(p.e_inc), allow_noconv=True)
@@ -639,15 +639,16 @@ def run_study(args):
     elif args.study == "disk":
         # Sec. 5.3.1, Table disk: 20 nm voxels, 220 nm slab, 400 nm bus, 200 nm
         # gap; reduced 1-level bus box + 2-level disk box with the modal M~
-        for r_um in (1, 2, 3, 4, 5):
+        for r_um in [float(v) for v in args.study_radii.split(",")]:
             p = inputs.disk_resonator(int(round(r_um / 0.02)), name=f"disk_r{r_um}")
-            row = {"radius_um": r_um, "grid": [p.nx, p.ny, p.nz]}
-            info = iters(p, homog=1, reduce_tol=1e-3, full=True)
+            row = {"radius_um": r_um, "grid": [p.nx, p.ny, p.nz], "homog": args.study_homog}
+            info = iters(p, homog=args.study_homog, reduce_tol=1e-3, max_iter=args.study_max_iter, full=True)
             row.update(prec_iters=info["iters_inner"], prec_relres=info["relres"],
                        build_s=round(info["t_setup_ms"] / 1e3, 3), prec_solve_s=round(secs[-1], 3),
                        precond_mb=round(info["precond_bytes"] / 2 ** 20, 1))
-            it0, r0 = iters(p, precond=vie.VIE_PREC_NONE, max_iter=6000)
-            row.update(noprec_iters=it0, noprec_relres=r0, noprec_solve_s=round(secs[-1], 3))
+            if not args.study_no_baseline:
+                it0, r0 = iters(p, precond=vie.VIE_PREC_NONE, max_iter=6000)
+                row.update(noprec_iters=it0, noprec_relres=r0, noprec_solve_s=round(secs[-1], 3))
             rows.append(row)
     else:
         for nx in (128, 256, 512, 1024, 2048):
@@ -656,7 +657,7 @@ def run_study(args):
             it1, r1 = iters(p)
             rows.append({"nx": nx, "length_um": nx * 0.025, "unpreconditioned_iters": it0, "relres0": r0,
                          "preconditioned_iters": it1, "relres1": r1})
-    print(json.dumps({"study": args.study, "tol": 1e-4, "precision": "fp64", "restart": 50,
+    print(json.dumps({"study": args.study, "tol": 1e-4, "precision": "fp64", "restart": args.study_restart,
                       "solve_seconds": [round(s, 3) for s in secs], "rows": rows}))
     return 0
 
@@ -695,6 +696,11 @@ def main():
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     ap.add_argument("--study", choices=["bragg", "length", "disk"], default=None,
                     help="qualitative iteration studies (prints one JSON line; not a bench line)")
+    ap.add_argument("--study-restart", type=int, default=50, help="GMRES restart length of the studies")
+    ap.add_argument("--study-radii", default="1,2,3,4,5", help="disk study: radii in um")
+    ap.add_argument("--study-homog", type=int, default=1, help="disk study: homogenisation variant (1 mode)")
+    ap.add_argument("--study-no-baseline", action="store_true", help="disk study: skip the unpreconditioned solves")
+    ap.add_argument("--study-max-iter", type=int, default=20000, help="disk study: cap of the preconditioned solves")
     args = ap.parse_args()
     if args.study:
         return run_study(args)

@@ -263,7 +263,10 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   d.nx = nx; d.ny = ny; d.nz = nz;
   d.L = embed_len(nx); d.Py = embed_len(ny); d.Pz = embed_len(nz);
   d.Lh = d.L / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
-  if ((long long)d.Py * d.Pz > 4096) { set_error("vie_plan_create: cross-section too large (Py*Pz > 4096)"); return VIE_EINVAL; }
+  if (d.Py > fft_max_len<double2>() || d.Pz > fft_max_len<double2>()) {
+    set_error("vie_plan_create: cross-section embedding %dx%d exceeds one shared-memory line", d.Py, d.Pz);
+    return VIE_EINVAL;
+  }
   if (3LL * nx * ny * nz >= (1LL << 31) - 64) {
     // the streaming kernels index a vector with 32-bit arithmetic
     set_error("vie_plan_create: 3*nx*ny*nz = %lld unknowns, the limit is 2^31 - 64", 3LL * nx * ny * nz);
@@ -275,6 +278,7 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   }
   for (const vie_box& b : P->boxes) {
     if (b.levels < 0 || b.levels > 2) { set_error("vie_plan_create: box levels must be 0, 1 or 2"); return VIE_EINVAL; }
+    if (P->opts.precond == VIE_PREC_NONE) continue;   // the boxes carry no blocks
     // the Chan eigenvalues are transformed in FP64; one split doubles the limit
     // (x-lines for every box, y-lines too for a 2-level box)
     for (int axis = 0; axis < (b.levels == 2 ? 2 : 1); ++axis) {
@@ -431,7 +435,7 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
   const double L = 2.0 * fft_next_smooth(nx), Py = 2.0 * fft_next_smooth(ny), Pz = 2.0 * fft_next_smooth(nz);
   const double spec = 6.0 * (L / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1) * (16 + 8);
   const double full = L * Py * Pz * 16;                  // spectra assembly scratch
-  const double T = 3.0 * Pz * Py * nx * (16 + 8);
+  const double T = 3.0 * Pz * Py * nx * (16 + 8) + ((double)Py * Pz > 4096 ? 3.0 * nz * Py * nx * (16 + 8) : 0);
   const double Sx = (3.0 * L * 16 > 200 * 1024) ? 3.0 * Pz * Py * L * (16 + 8) : 0;
   const double Xs = (L > 12736) ? 3.0 * Pz * Py * L * 16 + L * Py * Pz * 16 : 0;   // long-line split scratch
   const double vec = N * 3 * (16 * 6 + 8 * 8) + N * 24;

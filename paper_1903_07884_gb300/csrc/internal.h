@@ -87,6 +87,8 @@ struct vie_plan_s {
   vie::DevBuf T128, T64;               // [3][Pz][Py][nx] matvec intermediate
   vie::DevBuf S128, S64;               // [3][Pz][Py][L] full x-spectrum (unfused path only)
   vie::DevBuf X128, X64;               // split scratch for x-lines longer than shared memory
+  bool yz_split = false;               // Py*Pz > 4096: y and z transforms as separate line passes
+  vie::DevBuf U128, U64;               // [3][nz][Py][nx] y-spectrum of the unpadded z rows (yz_split)
   vie::DevBuf xin64, xout64;           // c64 staging for vie_matvec / precond (mixed)
   vie::DevBuf dev_err;                 // int: set by a kernel whose bounded wait ran out
   bool has_eps = false;

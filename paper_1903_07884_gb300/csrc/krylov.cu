@@ -68,6 +68,7 @@ struct Krylov {
   DevBuf partial;                 // double2 [NPART][PST]
   DevBuf state;                   // GmresDev
   DevBuf x128, r128, b128, d64, rhs64, r64, t128;
+  DevBuf xbest;                   // best iterate of a multi-cycle solve (allocated on first use)
   DevBuf scal;                    // double [8]: norms
   int* hflag = nullptr;           // pinned host mirror: done, iters
   cudaGraphExec_t g64 = nullptr, g128 = nullptr;
@@ -984,8 +985,14 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
   if (bnorm == 0.0) return VIE_OK;
   cudaGraphExec_t& gexec = KB<C>::g(K);
   int total = 0, cycles = 0;
-  double rr = 1.0, rr_best = 2.0;
+  double rr = 1.0, rr_best = 1.0;   // x0 = 0 has the residual ||b||
   int stalls = 0;
+  bool have_best = false;
+  C* xb = nullptr;
+  if (max_cycles > 1) {
+    if (K.xbest.bytes < sizeof(C) * n3) VIE_TRY(K.xbest.alloc(sizeof(C) * n3));
+    xb = K.xbest.as<C>();
+  }
   while (total < max_iter) {
     // cycle start from the current residual rwork
     k_norm_partial<C><<<NPART, RED_THREADS, 0, st>>>(rwork, n3, part);
@@ -1064,6 +1071,14 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
     total += hk;
     rr = hsc[1] / bnorm;
     if (rr <= tol || hk == 0) break;
+    // a cycle cannot raise the true residual in exact arithmetic (y = 0 is
+    // feasible), but on an ill-conditioned operator the basis can lose
+    // orthogonality and it does; the next cycle still starts from the new
+    // residual (a different Krylov space), and the best iterate is kept
+    if (rr < rr_best) {
+      VIE_CUDA(cudaMemcpyAsync(xb, x, sizeof(C) * n3, cudaMemcpyDeviceToDevice, st));
+      have_best = true;
+    }
     // restarted GMRES may converge slowly, but three cycles in a row that
     // do not improve the best residual by 1% mean stagnation (or the
     // rounding floor of this precision): stop and report the residual
@@ -1071,8 +1086,16 @@ static vie_status gmres(vie_plan_s* P, const C* rhs, C* x, C* rwork, double tol,
       if (++stalls >= 3) break;
     } else {
       stalls = 0;
-      rr_best = rr;
     }
+    rr_best = std::min(rr, rr_best);
+  }
+  if (rr > rr_best) {
+    // end on the best iterate (x0 = 0 when no cycle went below ||b||)
+    if (have_best) VIE_CUDA(cudaMemcpyAsync(x, xb, sizeof(C) * n3, cudaMemcpyDeviceToDevice, st));
+    else VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(C) * n3, st));
+    VIE_TRY(op_A<C>(P, x, w));
+    VIE_TRY(sub_same<C>(rhs, w, rwork, n3, st));
+    rr = rr_best;
   }
   *iters = total;
   *relres = rr;

@@ -23,6 +23,14 @@ vie_status matvec_alloc(vie_plan_s* P) {
   const size_t x64 = P->fused_x64 ? 0 : fft_scratch_elems<float2>(*P->fL, nl);
   if (x128) VIE_TRY(P->X128.alloc(sizeof(double2) * x128));
   if (x64) VIE_TRY(P->X64.alloc(sizeof(float2) * x64));
+  // cross-sections whose Py x Pz slab does not fit shared memory take the
+  // y- and z-transforms as separate line passes through U[3][nz][Py][nx]
+  P->yz_split = (long long)d.Py * d.Pz > 4096;
+  if (P->yz_split) {
+    const long long nU = 3LL * d.nz * d.Py * d.nx;
+    VIE_TRY(P->U128.alloc(sizeof(double2) * nU));
+    VIE_TRY(P->U64.alloc(sizeof(float2) * nU));
+  }
   const long long n3 = 3LL * d.nx * d.ny * d.nz;
   VIE_TRY(P->xin64.alloc(sizeof(float2) * n3));
   VIE_TRY(P->xout64.alloc(sizeof(float2) * n3));

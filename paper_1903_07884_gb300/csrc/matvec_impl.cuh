@@ -571,6 +571,16 @@ __global__ void __launch_bounds__(256) k_mv_yz_inv(const C* __restrict__ T, cons
       });
 }
 
+// epilogue of the split yz path: y holds G x on entry, y = x - M (x + G x)
+template <class C>
+__global__ void k_mv_epilogue(const C* __restrict__ x, const C* __restrict__ Mv, C* __restrict__ y, int nvox) {
+  const long long n3 = 3LL * nvox;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x) {
+    const C q = x[i];
+    y[i] = csub(q, cmul(Mv[i % nvox], cadd(q, y[i])));
+  }
+}
+
 static inline int pick_xg(const MvDims& d, size_t csize) {
   const size_t slab = (size_t)(d.Py * d.Pz + 1) * csize;
   int xg = 32;
@@ -618,7 +628,17 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   const int yzr = sizeof(C) == 8 ? ((d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0) : 0;
   const size_t smemR = (size_t)d.nz * YZ_XG * (d.Py + 1) * sizeof(float2);
   const dim3 gR(ceil_div(d.nx, YZ_XG), 3);
-  if (yzr) {
+  C* U = (C*)(sizeof(C) == 16 ? P->U128.p : P->U64.p);
+  const long long pyx = (long long)d.Py * d.nx;
+  if (P->yz_split) {
+    // y-lines of every (b, z) row (stride nx), padded to Py, into U; then
+    // z-lines of every (b, ky, x) (stride Py nx), padded to Pz, into T
+    LineDesc dy{d.ny, d.Py, 3 * d.nz * d.nx, d.nx, 3 * d.nz, 1, (long long)d.ny * d.nx, 0, d.nx,
+                1, pyx, 0, d.nx};
+    VIE_TRY(fft_lines<C>(x, U, dy, *P->fPy, -1, 1.0, nullptr, st));
+    LineDesc dz{d.nz, d.Pz, (int)(3 * pyx), (int)pyx, 3, 1, d.nz * pyx, 0, pyx, 1, d.Pz * pyx, 0, pyx};
+    VIE_TRY(fft_lines<C>(U, T, dz, *P->fPz, -1, 1.0, nullptr, st));
+  } else if (yzr) {
     Prof pf_("mv_yz_fwd_c64", st);
     if (yzr == 1) k_mv_yz_fwd_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
     else k_mv_yz_fwd_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
@@ -628,7 +648,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);
     k<<<gA, 256, smemA, st>>>(x, T, d, py, pz, XG);
   }
-  count_launch();
+  if (!P->yz_split) count_launch();
   VIE_CHECK_LAUNCH();
   // pass B
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
@@ -681,6 +701,20 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, X, st));
   }
   // pass C
+  if (P->yz_split) {
+    // inverse z-lines (keep z < nz) into U, inverse y-lines (keep y < ny) into
+    // y, then the epilogue; 1/(L Py Pz) is in the spectra
+    LineDesc iz{d.Pz, d.nz, (int)(3 * pyx), (int)pyx, 3, 1, d.Pz * pyx, 0, pyx, 1, d.nz * pyx, 0, pyx};
+    VIE_TRY(fft_lines<C>(T, U, iz, *P->fPz, +1, 1.0, nullptr, st));
+    LineDesc iy{d.Py, d.ny, 3 * d.nz * d.nx, d.nx, 3 * d.nz, 1, pyx, 0, d.nx, 1, (long long)d.ny * d.nx, 0, d.nx};
+    VIE_TRY(fft_lines<C>(U, y, iy, *P->fPy, +1, 1.0, nullptr, st));
+    const int nvox = d.nx * d.ny * d.nz;
+    Prof pf_(sizeof(C) == 8 ? "mv_epilogue_c64" : "mv_epilogue_c128", st);
+    k_mv_epilogue<C><<<(int)std::min<long long>((3LL * nvox + 255) / 256, 152LL * 8), 256, 0, st>>>(x, Mv, y, nvox);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+  }
   if (yzr) {
     Prof pf_("mv_yz_inv_c64", st);
     if (yzr == 1)

@@ -34,8 +34,11 @@ def _oracle_matvec(nx, ny, nz, h, k0, eps_bg, eps, x):
 
 @pytest.mark.parametrize("shape,eps_bg", [((1, 1, 1), 1.0), ((2, 1, 1), 1.0), ((3, 2, 2), 2.085), ((5, 3, 2), 1.0),
                                           ((7, 4, 3), 2.085), ((37, 5, 3), 1.0), ((64, 8, 4), 1.0),
-                                          ((33, 12, 2), 2.085)])
+                                          ((33, 12, 2), 2.085), ((6, 40, 40), 1.0), ((16, 100, 11), 2.085),
+                                          ((1, 130, 17), 1.0)])
 def test_matvec_fp64_matches_oracle(shape, eps_bg):
+    """The last three shapes have Py Pz > 4096 (separate y and z line passes;
+    (1, 130, 17) also a single x column, Py = 2 * 135 = 270)."""
     torch = cuda_or_fail()
     nx, ny, nz = shape
     h = 0.05
@@ -53,10 +56,12 @@ def test_matvec_fp64_matches_oracle(shape, eps_bg):
         assert relerr(y, op.dense_matvec(A, x)) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4), (1013, 3, 2)])
+@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4), (1013, 3, 2), (16, 100, 11), (1, 128, 33)])
 def test_matvec_mixed_matches_oracle(shape):
     """(1013, 3, 2): a ragged nx whose embedding is L = 2048, the compile-time
-    radix-16 x pass (zero padding and crop at a non-aligned edge)."""
+    radix-16 x pass (zero padding and crop at a non-aligned edge).  The last
+    two have Py Pz > 4096 (split y and z passes; with nx = 1 the y-lines of
+    Py = 256 are contiguous and take the warp-register FFT)."""
     cuda_or_fail()
     nx, ny, nz = shape
     eps = inputs.random_permittivity(nz, ny, nx, seed=11)
@@ -129,6 +134,9 @@ def _precond_case(name):
     if name == "two_level_even":
         p = inputs.straight_guide(32, 20, 4, 0.025, 1.55, core_ny=12, absorber=3)
         return dataclasses.replace(p, boxes=[(0, 0, 0, 32, 20, 4, 2)]), 0.0, 3
+    if name == "two_level_nz11":     # m2 = 33: two rows per lane, the disk's slab thickness
+        p = inputs.straight_guide(12, 10, 11, 0.02, 1.545, core_ny=6, absorber=2)
+        return dataclasses.replace(p, boxes=[(0, 0, 0, 12, 10, 11, 2)]), 0.0, 1
     if name == "two_level_m96":
         p = inputs.straight_guide(8, 6, 32, 0.025, 1.55, core_ny=4, core_nz=24, absorber=1)
         return dataclasses.replace(p, boxes=[(0, 0, 0, 8, 6, 32, 2)]), 0.0, 2
@@ -137,7 +145,7 @@ def _precond_case(name):
 
 @pytest.mark.parametrize("name", ["straight_full", "small_reduced", "prime_nx_bluestein", "bragg_boxes_mode",
                                   "coupler_boxes", "wide_box_m576", "disk_blocked_2level",
-                                  "two_level_prime_bluestein", "two_level_even", "two_level_m96"])
+                                  "two_level_prime_bluestein", "two_level_even", "two_level_nz11", "two_level_m96"])
 def test_precond_fp64_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
@@ -157,7 +165,7 @@ def test_precond_fp64_matches_oracle(name):
 
 @pytest.mark.parametrize("name", ["straight_full", "small_reduced", "bragg_boxes_mode", "wide_box_m576",
                                   "disk_blocked_2level", "two_level_prime_bluestein", "two_level_even",
-                                  "two_level_m96"])
+                                  "two_level_nz11", "two_level_m96"])
 def test_precond_mixed_matches_oracle(name):
     cuda_or_fail()
     p, tau, variant = _precond_case(name)
