@@ -678,6 +678,52 @@ def run_profile_case(args):
     return 0
 
 
+def run_precond2_case(args):
+    """Blocked disk preconditioner (reduced 1-level bus box + 2-level disk box,
+    3 um radius, 20 nm voxels, complex-FP32 apply): per-kernel device times of
+    10 applies after 3 warm-up applies, and the bandwidth the 2-level block
+    product reaches (its stored inverses, 22 801 blocks of 33 x 33, exceed L2).
+    Prints one JSON line (not a bench line)."""
+    import torch
+
+    from paper_1903_07884_gb300 import inputs, vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+    p = inputs.disk_resonator(150)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=1e-3, homog=1)
+    plan.set_permittivity(to_device(p.eps))
+    plan.build()
+    r = to_device(inputs.random_field((3, p.nz, p.ny, p.nx), seed=5))
+    for _ in range(3):
+        plan.precond(r, vie.VIE_MIXED)
+    torch.cuda.synchronize()
+    reps = 10
+    vie.vie_profile_reset()
+    vie.vie_profile_enable(True)
+    for _ in range(reps):
+        plan.precond(r, vie.VIE_MIXED)
+    torch.cuda.synchronize()
+    vie.vie_profile_enable(False)
+    table = vie.profile_table()
+    vie.vie_profile_reset()
+    plan.close()
+    _, _, _, n, ny, nz, _ = p.boxes[1]
+    m2 = 3 * nz
+    slots = (n // 2 + 1) * (ny // 2 + 1)
+    algo = 8 * (slots * m2 * m2 + 2 * m2 * n * ny)     # inverses once, spectra in and out once
+    launches, tot = table["block_gemv2_c64"]
+    per_ms = tot / launches
+    pk, pk_src = peaks()
+    ach = algo / (per_ms * 1e-3) / 1e9
+    print(json.dumps({"precond2_case": f"disk r=3um {p.nx}x{p.ny}x{p.nz}, disk box {n}x{ny}x{nz}",
+                      "block_gemv2_c64": {"launches": launches, "avg_ms": round(per_ms, 5),
+                                          "algorithmic_bytes": algo, "achieved_gbs": round(ach, 1),
+                                          "peak_gbs": pk["hbm_gbs"], "peak_source": pk_src,
+                                          "frac": round(ach / pk["hbm_gbs"], 3)},
+                      "apply_kernels_ms_per_apply": {k: round(v[1] / reps, 4) for k, v in
+                                                     sorted(table.items(), key=lambda kv: -kv[1][1])}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,6 +742,8 @@ def main():
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     ap.add_argument("--study", choices=["bragg", "length", "disk"], default=None,
                     help="qualitative iteration studies (prints one JSON line; not a bench line)")
+    ap.add_argument("--precond2-case", action="store_true",
+                    help="time the blocked 2-level preconditioner apply of a 3 um disk (prints no bench line)")
     ap.add_argument("--study-restart", type=int, default=50, help="GMRES restart length of the studies")
     ap.add_argument("--study-radii", default="1,2,3,4,5", help="disk study: radii in um")
     ap.add_argument("--study-homog", type=int, default=1, help="disk study: homogenisation variant (1 mode)")
@@ -706,6 +754,8 @@ def main():
         return run_study(args)
     if args.profile_case:
         return run_profile_case(args)
+    if args.precond2_case:
+        return run_precond2_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -98,6 +98,7 @@ __global__ void k_block_assemble2(double2* __restrict__ D, const double2* __rest
 // Sy and (n-f, ny-g) with Sx Sy.  R, Z: [m2][ny][n] spectra; invT: column-major
 // D^{-1} per block.  Lane i owns rows i, i + 32, ... (RPL rows).
 constexpr int G2_WARPS = 8;
+constexpr int G2_JB = 8;
 template <class C, int RPL>
 __global__ void __launch_bounds__(G2_WARPS * 32) k_block_gemv2(const C* __restrict__ invT, const C* __restrict__ R,
                                                               C* __restrict__ Z, int n, int ny, int nz, int nfs,
@@ -129,21 +130,33 @@ __global__ void __launch_bounds__(G2_WARPS * 32) k_block_gemv2(const C* __restri
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = czero<C>();
   const C* D = invT + (long long)s * m2 * m2;
-  for (int j = 0; j < m2; ++j) {
-    const C r0 = rv[j];
-    const C r1 = hx ? rv[m2 + j] : czero<C>();
-    const C r2 = hy ? rv[2 * m2 + j] : czero<C>();
-    const C r3 = (hx && hy) ? rv[3 * m2 + j] : czero<C>();
-    const C* col = D + (long long)j * m2;
+  // G2_JB columns per batch: all their loads are issued before the first
+  // product, so a warp keeps G2_JB * RPL loads in flight instead of one
+  for (int j0 = 0; j0 < m2; j0 += G2_JB) {
+    C dv[G2_JB][RPL];
 #pragma unroll
-    for (int u = 0; u < RPL; ++u) {
-      const int i = lane + 32 * u;
-      if (i < m2) {
-        const C d = col[i];
-        cfma(acc[u][0], d, r0);
-        cfma(acc[u][1], d, r1);
-        cfma(acc[u][2], d, r2);
-        cfma(acc[u][3], d, r3);
+    for (int jj = 0; jj < G2_JB; ++jj) {
+      const int j = j0 + jj;
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int i = lane + 32 * u;
+        dv[jj][u] = (j < m2 && i < m2) ? D[(long long)j * m2 + i] : czero<C>();
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < G2_JB; ++jj) {
+      const int j = j0 + jj;
+      if (j >= m2) break;
+      const C r0 = rv[j];
+      const C r1 = hx ? rv[m2 + j] : czero<C>();
+      const C r2 = hy ? rv[2 * m2 + j] : czero<C>();
+      const C r3 = (hx && hy) ? rv[3 * m2 + j] : czero<C>();
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        cfma(acc[u][0], dv[jj][u], r0);
+        cfma(acc[u][1], dv[jj][u], r1);
+        cfma(acc[u][2], dv[jj][u], r2);
+        cfma(acc[u][3], dv[jj][u], r3);
       }
     }
   }
