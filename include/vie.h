@@ -117,8 +117,14 @@ void vie_default_opts(vie_opts* opts);
  * stores their circulant-embedding spectra (the O(6n) storage of the remark
  * after Eq. sys_mat).  cuda_stream: a cudaStream_t or NULL.  opts may be
  * NULL (defaults).  Boxes must lie inside the grid and not overlap.
- * Errors: VIE_EINVAL for non-positive sizes, h, k0 or eps_bg, or boxes out of
- * range / overlapping; VIE_ENOMEM if device memory runs out. */
+ * Cross-sections whose embedding Py x Pz exceeds 4096 points take the y and z
+ * transforms of the matvec as separate line passes (one more work array).
+ * Errors: VIE_EINVAL for non-positive sizes, h, k0 or eps_bg, boxes out of
+ * range / overlapping, box levels outside 0..2, 3*nx*ny*nz >= 2^31 - 64, an
+ * embedding or box length beyond the transform limits, and, when a
+ * preconditioner is requested, a 1-level box with 3 ny nz > 864 or a 2-level
+ * box with nz > 32 or (nx/2+1)(ny/2+1) > 65535; VIE_ENOMEM if device memory
+ * runs out. */
 vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double eps_bg,
                            const vie_opts* opts, void* cuda_stream, vie_plan_t* out);
 

@@ -37,3 +37,35 @@ def test_default_opts_and_estimate_without_gpu():
     assert abs(o.reduce_tol - 1e-3) < 1e-18
     est = vie.vie_estimate_bytes(1024, 16, 8, o)
     assert 1e8 < est < 2e10
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/vie.h, in order."""
+    text = open(os.path.join(ROOT, "include", "vie.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef\s+struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int x0, y0, z0" or "const vie_box* boxes"
+        head, *rest = [s.strip() for s in decl.split(",")]
+        fields.append(re.findall(r"[A-Za-z_][A-Za-z_0-9]*", head)[-1])
+        fields.extend(re.findall(r"[A-Za-z_][A-Za-z_0-9]*", r)[-1] for r in rest)
+    return fields
+
+
+def test_ctypes_structs_match_the_header():
+    """The binding's structs list the header's fields in the same order (a
+    field added on one side only would shift every later field)."""
+    for cls in (vie.vie_box, vie.vie_opts, vie.vie_info):
+        assert [f for f, _ in cls._fields_] == _header_struct_fields(cls.__name__), cls.__name__
+
+
+def test_box_tuples_of_six_or_seven_values():
+    """A 6-tuple box is a 1-level box (levels 0); the 7th value selects the level."""
+    b6 = vie.vie_box(*(1, 2, 3, 4, 5, 6))
+    b7 = vie.vie_box(*(1, 2, 3, 4, 5, 6, 2))
+    assert (b6.nz, b6.levels) == (6, 0) and b7.levels == 2
