@@ -182,6 +182,31 @@ TRAFFIC = {
 }
 
 
+MV_KERNELS = ("mv_yz_fwd_c64", "mv_x_c64", "mv_yz_inv_c64")
+
+
+def matvec_summary(table: dict, p, hbm_gbs: float):
+    """Complex-FP32 matvec bandwidth from the per-kernel table of a profiled
+    solve ({kernel: (launches, total ms)}): the three passes each launch once
+    per matvec.  Two byte counts: the floor the method must move (x and y,
+    M, the stored spectrum octants once) and the three-pass traffic that adds
+    the yz-transformed intermediate T (written, read and written, read)."""
+    if not all(k in table and table[k][0] > 0 for k in MV_KERNELS):
+        return None
+    per = {k: table[k][1] / table[k][0] for k in MV_KERNELS}
+    ms = sum(per.values())
+    nx, ny, nz = p.nx, p.ny, p.nz
+    N = nx * ny * nz
+    L, Py, Pz = 2 * _smooth(nx), 2 * _smooth(ny), 2 * _smooth(nz)
+    oct_ = 6 * (L // 2 + 1) * (Py // 2 + 1) * (Pz // 2 + 1)
+    floor = 8 * (7 * N + oct_)
+    three = sum(algorithmic(k, p, {})[1] for k in MV_KERNELS)
+    gbs = lambda b: b / (ms * 1e-3) / 1e9
+    return {"ms_per_matvec": ms, "kernels_ms": per, "floor_bytes": floor, "floor_gbs": gbs(floor),
+            "three_pass_bytes": three, "three_pass_gbs": gbs(three), "frac_three_pass": gbs(three) / hbm_gbs,
+            "peak_gbs": hbm_gbs}
+
+
 def traffic(kernel: str, wname: str, plan_meta: dict):
     t = TRAFFIC.get(wname, {}).get(kernel)
     if t is None:
@@ -462,6 +487,7 @@ def run_gpu(args):
             "e2e": {"value": solves_per_s(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": int(16 * N + 16 * 3 * N), "d2h_bytes_per_step": int(16 * 3 * N)},
             "roofline": roof,
+            "matvec": matvec_summary(table, p, pk["hbm_gbs"]),
             "profile_ms": {k: round(v[1], 4) for k, v in top[:12]}}
     plan.close()
 
