@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import circulant, gmres
+from oracle import circulant, gmres, homogenize
 from oracle import operator as op
 from oracle import precond as pc
 from oracle import precond2 as pc2
@@ -163,3 +163,34 @@ def test_two_level_preconditioned_gmres_solves_the_system():
     res = gmres.gmres(lambda v: (A @ v.ravel()).reshape(v.shape), b, P.apply, tol=1e-12)
     assert res.relres <= 1e-12
     np.testing.assert_allclose(res.x.ravel(), np.linalg.solve(A, b.ravel()), atol=1e-10 * np.abs(b).max())
+
+
+def test_plane_homogenisation_hand_example():
+    """Plane variants of M~ (reading R12) on a 2 x 2 x 3 box written out by hand:
+    plane z = 0 holds 1, 1, 1, 1+4j, 0, 0 -> mean (4 + 4j)/6; plane z = 1 is
+    all 2 -> mean 2; the mode over the box is 2 (six entries)."""
+    M = np.zeros((2, 2, 3), dtype=complex)
+    M[0] = [[1, 1, 1], [1 + 4j, 0, 0]]
+    M[1] = 2.0
+    np.testing.assert_allclose(homogenize.homogenize_plane(M, 2), [(4 + 4j) / 6, 2.0])
+    np.testing.assert_allclose(homogenize.homogenize_plane(M, 3), [4 / 6, 2.0])
+    np.testing.assert_allclose(homogenize.homogenize_plane(M, 1), [2.0, 2.0])
+
+
+def test_disk_geometry():
+    """Synthetic disk beside a bus (Sec. 5.3.1): the disk covers about pi/4 of
+    its box, the bus is one full-length core, the boxes are disjoint and inside
+    the grid, the disk box is 2-level, and the disk stays lossless."""
+    R = 40
+    p = inputs.disk_resonator(R, nz=3, lead=10)
+    bus, disk = p.boxes
+    assert disk[6] == 2 and len(bus) == 6
+    for b in (bus, disk):
+        x0, y0, z0, bx, by, bz = b[:6]
+        assert x0 >= 0 and y0 >= 0 and x0 + bx <= p.nx and y0 + by <= p.ny and z0 + bz <= p.nz
+    assert bus[1] + bus[4] <= disk[1]                          # the gap separates them in y
+    x0, y0, _, bx, by, _ = disk[:6]
+    core = p.eps[1, y0:y0 + by, x0:x0 + bx].real > 3
+    assert abs(core.mean() - math.pi / 4) < 0.02
+    assert np.all(p.eps[:, y0:y0 + by, x0:x0 + bx].imag == 0)
+    assert np.all(p.eps[1, bus[1]:bus[1] + bus[4], :].real > 3)
