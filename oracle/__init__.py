@@ -16,6 +16,11 @@ Parity status per function (see the pin tests in tests/test_oracle_*.py):
   greens.entries / self_term      pinned (finite differences, quadrature,
                                    static limit, trace identity, parity)
   operator.dense_matrix           pinned (symmetry, single voxel closed form)
+  operator.material / rhs         pinned (Table 1 contrasts; the single voxel's
+                                   static limit is the Clausius-Mossotti factor)
+  operator.background_k           pinned (the cladding wavelength lambda0 /
+                                   sqrt(eps_b) puts whole periods of phase
+                                   between the radiating traces)
   operator.fft_matvec             pinned (equals dense on brute-force grids)
   circulant.*                     pinned (Eq. Chan hand example, Frobenius
                                    optimality, eigen-decomposition)

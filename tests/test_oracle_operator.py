@@ -82,3 +82,58 @@ def test_cladding_rows_are_identity():
     y = op.fft_matvec(x, M, op.generator_spectra(p.nx, p.ny, p.nz, p.h, k))
     clad = np.broadcast_to(M == 0, x.shape)
     np.testing.assert_array_equal(y[clad], x[clad])
+
+
+# --- pins of the material operator, the right-hand side and the background
+# wavenumber against values fixed outside the oracle's own formulas ---------
+
+def test_material_recovers_table1_contrasts():
+    """Table 1 prints the contrasts the problem is posed with: Si in SiO2 is
+    12.1/2.085 ~ 5.80 and Si3N4 in SiO2 is 3.99/2.085 ~ 1.91; materials on
+    their own are cladded by air.  M = (eps_r - 1)/eps_r inverts to
+    eps_r = 1/(1 - M), which must reproduce those printed contrasts (a missing
+    division by the background, or a dropped 1/eps_r, does not)."""
+    for eps, eps_bg, printed in ((12.1, 2.085, 5.80), (3.99, 2.085, 1.91), (12.1, 1.0, 12.1),
+                                 (2.085, 1.0, 2.085)):
+        M = op.material(np.array([[[eps]]], dtype=np.complex128), eps_bg)[0, 0, 0]
+        assert abs(1.0 / (1.0 - M) - printed) < 0.006, (eps, eps_bg)
+    # the cladding itself is no contrast at all: M = 0, hence b = 0 there
+    assert op.material(np.array([[[2.085 + 0j]]]), 2.085)[0, 0, 0] == 0.0
+
+
+def test_single_voxel_static_limit_is_clausius_mossotti():
+    """A lone voxel at k0 -> 0 is a small dielectric sphere (the self term is
+    the equal-volume sphere's) in a uniform field.  Electrostatics gives its
+    interior field 3 E0 / (eps_r + 2) with eps_r relative to the background,
+    and Sec. 2 (j = j omega eps0 (eps_r - 1) e) makes the normalised current
+    w = (eps_r - 1) e, so w = 3 (eps_r - 1)/(eps_r + 2) e_inc: the
+    Clausius-Mossotti factor.  Pins material, rhs and the system together."""
+    eps_bg = 2.085
+    eps = np.array([[[12.11 - 0.4j]]])
+    e = np.array([0.3 - 0.2j, 1.0 + 0.1j, -0.5j]).reshape(3, 1, 1, 1)
+    k = op.background_k(0.0, eps_bg)
+    M = op.material(eps, eps_bg)
+    A = op.dense_matrix(1, 1, 1, H, k, M)
+    w = np.linalg.solve(A, op.rhs(eps, eps_bg, e).ravel())
+    er = (12.11 - 0.4j) / eps_bg
+    np.testing.assert_allclose(w, 3 * (er - 1) / (er + 2) * e.ravel(), rtol=1e-14)
+
+
+def test_background_wavenumber_sets_the_wavelength_in_the_cladding():
+    """In a background of permittivity eps_b the wavelength is
+    lambda_b = lambda0 / sqrt(eps_b).  With voxels of lambda_b / 20, the
+    radiating trace sum_a G^{aa}(d) = 2 k^2 V exp(-jkR)/(4 pi R) at R =
+    lambda_b and R = 2 lambda_b differ by the factor 1/2 exactly (a whole
+    period of phase apart); any other k leaves a phase between them."""
+    lam0, eps_bg = 1.55, 2.085
+    lam_b = lam0 / math.sqrt(eps_bg)
+    h = lam_b / 20
+    k = op.background_k(2 * math.pi / lam0, eps_bg)
+    G = greens.entries(np.array([20, 40]), np.array([0, 0]), np.array([0, 0]), h, k)
+    tr = G[greens.pair_index(0, 0)] + G[greens.pair_index(1, 1)] + G[greens.pair_index(2, 2)]
+    ratio = tr[1] / tr[0]
+    assert abs(ratio - 0.5) < 1e-12
+    # the same voxels in vacuum at the same lambda0 are not a whole period apart
+    G0 = greens.entries(np.array([20, 40]), np.array([0, 0]), np.array([0, 0]), h, 2 * math.pi / lam0)
+    tr0 = G0[0] + G0[3] + G0[5]
+    assert abs(tr0[1] / tr0[0] - 0.5) > 0.1
