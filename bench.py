@@ -169,7 +169,7 @@ def algorithmic(kernel: str, p, plan_meta: dict):
 
 
 # DRAM bytes per launch from the ncu step capture of the same kernel versions
-# (profiles/ncu_gmres_step_long_straight_1024x16x8.md, 1024x16x8 wire):
+# (the --set full capture of one GMRES step of the 1024x16x8 wire):
 # per basis column read for the Arnoldi kernels (120.4 MB at j = 36, 38
 # columns), per launch for the others.  Cleared whenever a kernel changes.
 TRAFFIC = {
@@ -240,6 +240,27 @@ def oracle_iterations(wname: str, tol: float):
     return None, None
 
 
+def oracle_solution(wname: str):
+    """The oracle's stored solution of the workload (written by
+    tests/golden/make_oracle_solutions.py, oracle GMRES to 1e-12), or None."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "oracle_solutions.json")
+    if not os.path.exists(path):
+        return None
+    meta = json.load(open(path)).get(wname)
+    if not meta or "sample" in meta:
+        return None
+    return np.load(os.path.join(ROOT, "tests", "golden", meta["file"]))
+
+
+def solution_errors(w, ref) -> dict:
+    """Relative 2-norm error and element-wise error (against the largest
+    entry of the reference) of a solution."""
+    import numpy as np
+    return {"rel_err": float(np.linalg.norm(w - ref) / np.linalg.norm(ref)),
+            "max_err": float(np.abs(w - ref).max() / np.abs(ref).max())}
+
+
 class OracleSample:
     """Times the oracle's setup (generator spectra + full preconditioner
     build) once and its per-iteration work (FFT matvec, preconditioner apply,
@@ -270,6 +291,18 @@ class OracleSample:
         for i in range(self.V.shape[0]):
             h = np.vdot(self.V[i], w)
             w = w - h * self.V[i]
+        return time.perf_counter() - t0
+
+    def cycle(self, restart: int = 50) -> float:
+        """Seconds of one full GMRES(restart) cycle of the oracle's own solver
+        (oracle.gmres, right-preconditioned, from x = 0): restart iterations
+        with the growing modified Gram-Schmidt, the cycle's update and its
+        true-residual check."""
+        from oracle import gmres as og
+        from oracle import operator as op
+        t0 = time.perf_counter()
+        og.gmres(lambda v: op.fft_matvec(v, self.M, self.spec), self.b, self.P.apply, tol=1e-30,
+                 restart=restart, max_iter=restart)
         return time.perf_counter() - t0
 
     def residual(self, w_gpu) -> float:
@@ -312,7 +345,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_it, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": wname, "precision": "fp64 (CPU oracle)", "tol": args.tol},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle_model", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -492,21 +525,30 @@ def run_gpu(args):
     plan.close()
 
     if args.serving_n > 0:
-        line["serving"] = run_serving(args.serving_n, args.inflight, args.budget_gb, args.tol, args.fp64_serial_s)
+        line["serving"] = run_serving(args.serving_n, args.inflight, args.budget_gb, args.tol, args.fp64_serial_s,
+                                      args.fp64_serial_n)
 
+    ref = oracle_solution(wname)
+    if ref is not None:
+        line["accuracy"] = {"vs_oracle_solution": "tests/golden (oracle GMRES to relres 1e-12)",
+                            "mixed": solution_errors(w_mixed, ref), "fp64_gpu": solution_errors(w64, ref)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S = OracleSample(p)
-        ts = [S.iteration() for _ in range(3)]
+        restart = 50
+        t_cyc = S.cycle(restart)
         iters, src = oracle_iterations(wname, args.tol)
         if iters is None:
-            iters, src = infos[-1]["iters_inner"], "iteration count of the GPU solve"
-        t_solve = S.t_setup + iters * statistics.mean(ts)
+            iters, src = infos[-1]["iters_inner"], "iteration count of the GPU FP64 solve"
+        t_solve = S.t_setup + (iters / restart) * t_cyc
         line["cpu_baseline"] = {
             "value": 1.0 / t_solve, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": (f"oracle setup {S.t_setup:.2f} s (spectra + preconditioner build) + 3 iteration samples "
-                       f"(mean {statistics.mean(ts):.3f} s); one solve = setup + {iters} iterations ({src})")}
-        line["accuracy"] = {"oracle_relres_of_mixed_solution": S.residual(w_mixed),
-                            "oracle_relres_of_fp64_solution": S.residual(w64)}
+            "sample": (f"the oracle's own solve of this workload, timed: setup {S.t_setup:.2f} s (generator spectra "
+                       f"+ preconditioner build) and its first full GMRES({restart}) restart cycle {t_cyc:.2f} s "
+                       f"({restart} iterations with the growing MGS, update and true residual); one solve = setup + "
+                       f"{iters}/{restart} cycles ({iters} iterations: {src})")}
+        acc = line.setdefault("accuracy", {})
+        acc["oracle_relres_of_mixed_solution"] = S.residual(w_mixed)
+        acc["oracle_relres_of_fp64_solution"] = S.residual(w64)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -514,7 +556,7 @@ def run_gpu(args):
     return 0
 
 
-def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_limit_s: float):
+def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_limit_s: float, fp64_n: int = 16):
     """Replay the first n_req requests of the seeded serving stream (Poisson
     arrivals, 50/s) against the continuous-batching server; every request is
     submitted at its arrival time with host buffers and its latency runs from
@@ -568,13 +610,16 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
            "p99_ms": float(np.percentile(lat, 99)), "max_inflight": inflight, "budget_gb": budget_gb,
            "mean_iters": float(np.mean([infos[i].iters_inner for i in infos])) if infos else None,
            "max_relres": float(max(infos[i].relres for i in infos)) if infos else None}
-    # plain FP64 GPU method, serially, same requests
-    lat64 = []
+    out["relres_all"] = "every served result's FP64 relative residual is <= max_relres"
+    # plain FP64 GPU method, serially, on the first requests of the same stream
+    # (at most fp64_n, time-bounded); each served result of those requests is
+    # compared with its FP64 solution
+    lat64, errs = [], []
     t_start = time.perf_counter()
-    for i, p in enumerate(probs):
+    for i, p in enumerate(probs[:fp64_n]):
         if time.perf_counter() - t_start > fp64_limit_s:
             break
-        eps, e, _ = bufs[i]
+        eps, e, w_srv = bufs[i]
         w = np.empty(p.e_inc.shape, dtype=np.complex128)
         opts = make_opts(precision=vie.VIE_FP64, tol=tol, boxes=p.boxes or None, homog=p.homog)
         ts = time.perf_counter()
@@ -582,10 +627,15 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
         vie.vie_solve_host(plan, eps.ctypes.data, e.ctypes.data, w.ctypes.data, allow_noconv=True)
         vie.vie_plan_destroy(plan)
         lat64.append(1000.0 * (time.perf_counter() - ts))
+        if status.get(i) in (vie.VIE_OK, vie.VIE_ENOCONV):
+            errs.append(float(np.linalg.norm(w_srv - w) / np.linalg.norm(w)))
     if lat64:
         out["fp64_serial"] = {"requests": len(lat64), "solves_per_s": len(lat64) / (sum(lat64) / 1000.0),
                               "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
+                              "time_bound_s": fp64_limit_s,
                               "note": "each request alone, no queueing; first requests of the same stream"}
+        out["max_rel_err_vs_fp64"] = max(errs) if errs else None
+        out["rel_err_vs_fp64_requests"] = len(errs)
     return out
 
 
@@ -763,7 +813,8 @@ def main():
     ap.add_argument("--serving-n", type=int, default=16, help="requests of the serving stream to replay (0 = skip)")
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=200.0)
-    ap.add_argument("--fp64-serial-s", type=float, default=30.0)
+    ap.add_argument("--fp64-serial-s", type=float, default=30.0, help="time bound of the serial FP64 serving leg")
+    ap.add_argument("--fp64-serial-n", type=int, default=16, help="requests of the serial FP64 serving leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     ap.add_argument("--study", choices=["bragg", "length", "disk"], default=None,

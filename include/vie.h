@@ -23,9 +23,11 @@
  * the device that is current when the plan is created, allocated and freed by
  * the caller.  "host" pointers are ordinary (preferably pinned) host memory.
  * The library owns everything inside a plan (generator spectra, material
- * arrays, preconditioner blocks, Krylov workspace); it allocates only in
- * vie_plan_create, vie_build_preconditioner and vie_server_* calls, never
- * inside vie_matvec / vie_precond_apply / vie_solve.
+ * arrays, preconditioner blocks, Krylov workspace); it allocates device
+ * memory in vie_plan_create, vie_build_preconditioner, the first vie_solve of
+ * a plan (Krylov workspace), the first vie_solve_host of a plan (its three
+ * staging buffers) and the vie_server_* calls, and never inside vie_matvec /
+ * vie_precond_apply or later solves of the same plan.
  *
  * Streams: every call enqueues its GPU work on the stream given at plan
  * creation (NULL = legacy default stream).  vie_matvec and vie_precond_apply
@@ -87,6 +89,9 @@ typedef struct {
   double reduce_tol;      /* memory reduction threshold tau (Sec. 5.1.1); 0 = off   */
   const vie_box* boxes;   /* partition boxes (copied at plan creation); NULL = one  */
   int nboxes;             /*   box covering the whole grid                          */
+  int inner_restart;      /* mixed: length of each complex-FP32 GMRES cycle; 0 =   */
+                          /*   min(2 restart, 128), the FP64 GMRES(restart) basis  */
+                          /*   bytes in complex FP32                                */
 } vie_opts;
 
 typedef struct {
@@ -108,7 +113,7 @@ typedef struct vie_plan_s* vie_plan_t;
 
 /* Fill *opts with the defaults: restart 50, tol 1e-9, max_iter 5000,
  * inner_tol 1e-6, max_refine 1000, VIE_MIXED, VIE_PREC_CIRCULANT,
- * VIE_HOM_REALMEAN, reduce_tol 1e-3, whole-grid box. */
+ * VIE_HOM_REALMEAN, reduce_tol 1e-3, whole-grid box, inner_restart 0. */
 void vie_default_opts(vie_opts* opts);
 
 /* Create a plan for an nx*ny*nz grid of voxel edge h (same length unit as
@@ -167,21 +172,34 @@ vie_status vie_precond_apply(vie_plan_t plan, const void* r_dev, void* z_dev, in
 vie_status vie_solve(vie_plan_t plan, const void* e_inc_dev, void* w_out_dev, vie_info* info);
 
 /* As vie_set_permittivity + vie_solve, with host buffers: copies eps and
- * e_inc to the device, solves and copies w back (host, double2 arrays). */
+ * e_inc to the device, solves and copies w back (host, double2 arrays).
+ * The first call on a plan allocates three device staging buffers (eps,
+ * e_inc and w: 7 N complex FP64 values); the plan keeps them for later
+ * calls and frees them in vie_plan_destroy. */
 vie_status vie_solve_host(vie_plan_t plan, const void* eps_host, const void* e_inc_host,
                           void* w_out_host, vie_info* info);
 
-/* Solve n independent problems (each plan already has its permittivity),
- * overlapping them on the device: plan i's work runs on its own stream.
- * e_inc[i], w_out[i] are device pointers; info may be NULL or an array of n.
- * Returns the most severe status. */
+/* Solve n independent problems (each plan already has its permittivity; all
+ * plans on the current device, each at most once) in lockstep: their GMRES
+ * runs advance together, one captured step graph per set of plans holds
+ * each plan's preconditioner and matvec as parallel branches and then the
+ * Arnoldi step kernels as single launches over a work-list of all plans of
+ * a precision, so plans of different lengths, cross-sections, precisions
+ * and options batch together.  A plan's host-side work between cycles runs
+ * on its own stream.  Each result is bitwise the result of vie_solve on that
+ * plan alone.  e_inc[i], w_out[i] are device pointers; info may be NULL or
+ * an array of n.  Returns the most severe status. */
 vie_status vie_solve_batch(vie_plan_t* plans, int n, const void* const* e_inc_dev,
                            void* const* w_out_dev, vie_info* info);
 
-/* Continuous-batching server.  Requests are admitted while their estimated
- * device footprint fits in budget_bytes and fewer than max_inflight are
- * running; each admitted request runs on its own stream/worker and overlaps
- * the others.  A request that can never fit is rejected (VIE_EREJECTED). */
+/* Continuous-batching server.  Requests are admitted in arrival order while
+ * their estimated device footprint fits in budget_bytes and fewer than
+ * max_inflight (1..256) are admitted.  Up to four worker threads prepare
+ * admitted requests (plan, upload, preconditioner); one driver thread keeps
+ * all prepared requests in one lockstep set (as vie_solve_batch), which
+ * requests join between chunks of steps as they become ready and leave as
+ * they finish.  Each result equals the request's vie_solve result bitwise.
+ * A request that can never fit is rejected (VIE_EREJECTED). */
 typedef struct vie_server_s* vie_server_t;
 
 vie_status vie_server_create(size_t budget_bytes, int max_inflight, vie_server_t* out);
@@ -218,17 +236,18 @@ void vie_server_destroy(vie_server_t srv);
  * vie_matvec(plan, x, y, VIE_FP64) for a plan with this grid, voxel size,
  * wavenumber, background and permittivity, from the caller's buffers only:
  * eps_dev [nz][ny][nx], x_dev and y_dev [3][nz][ny][nx] (device, double2;
- * x and y may not alias), cuda_stream a cudaStream_t or NULL.  Every
- * temporary lives in one file-scope device array of 64 MiB inside libvie
- * (held by each GPU from the first call -- or from context creation under
- * eager module loading -- until the process exits); grids that need more,
- * or whose x-embedding exceeds 4266 points (nx > 2130) or whose Py*Pz
- * exceeds 4096, are rejected with VIE_EINVAL and a message.  The first call
- * on a device resolves the array's device address with that device current;
- * make that first call before any stream capture.  All calls share the
- * array: calls whose GPU work overlaps (other streams or threads) race and
- * corrupt each other's results.  Calls no cudaMalloc / cudaFree.
- * Asynchronous on cuda_stream. */
+ * y may not overlap x or eps in any byte: VIE_EINVAL), cuda_stream a
+ * cudaStream_t or NULL.  Every temporary lives in one file-scope device
+ * array of 64 MiB inside libvie (held by each GPU from the first call -- or
+ * from context creation under eager module loading -- until the process
+ * exits); grids that need more, or whose x-embedding exceeds 4266 points
+ * (nx > 2130) or whose Py*Pz exceeds 4096, are rejected with VIE_EINVAL and
+ * a message.  Every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress); under lazy module loading the first call on
+ * a device also loads libvie's device code there, so make that first call
+ * before any stream capture.  All calls share the array: calls whose GPU
+ * work overlaps (other streams or threads) race and corrupt each other's
+ * results.  Calls no cudaMalloc / cudaFree.  Asynchronous on cuda_stream. */
 vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double eps_bg, const void* eps_dev,
                              const void* x_dev, void* y_dev, void* cuda_stream);
 

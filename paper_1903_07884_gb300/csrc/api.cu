@@ -51,11 +51,9 @@ void DevBuf::release() {
   bytes = 0;
 }
 
-struct StreamScope {
-  cudaStream_t prev;
-  explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
-  ~StreamScope() { g_alloc_stream = prev; }
-};
+cudaStream_t alloc_stream() { return g_alloc_stream; }
+void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
+using StreamScope = AllocScope;
 
 static std::once_flag g_pool_once;
 static void init_pool() {
@@ -175,6 +173,7 @@ void vie_default_opts(vie_opts* o) {
   o->reduce_tol = 1e-3;
   o->boxes = nullptr;
   o->nboxes = 0;
+  o->inner_restart = 0;
 }
 
 const char* vie_last_error(void) { return g_err; }
@@ -247,7 +246,8 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   if (o.restart < 1 || o.restart > 128 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 1 ||
       (o.precision != VIE_FP64 && o.precision != VIE_MIXED) ||
       (o.precond != VIE_PREC_NONE && o.precond != VIE_PREC_CIRCULANT) || o.homog < 1 || o.homog > 3 ||
-      !(o.reduce_tol >= 0) || !(o.inner_tol > 0) || o.nboxes < 0 || (o.nboxes > 0 && !o.boxes)) {
+      !(o.reduce_tol >= 0) || !(o.inner_tol > 0) || o.nboxes < 0 || (o.nboxes > 0 && !o.boxes) ||
+      o.inner_restart < 0 || o.inner_restart > 128) {
     set_error("vie_plan_create: invalid options");
     return VIE_EINVAL;
   }
@@ -393,10 +393,11 @@ vie_status vie_solve_host(vie_plan_t P, const void* eps_host, const void* e_inc_
   if (!P || !eps_host || !e_inc_host || !w_out_host) { set_error("vie_solve_host: NULL argument"); return VIE_EINVAL; }
   StreamScope scope(P->st);
   const long long N = (long long)P->nx * P->ny * P->nz;
-  DevBuf eps, e, w;
-  VIE_TRY(eps.alloc(sizeof(double2) * N));
-  VIE_TRY(e.alloc(sizeof(double2) * 3 * N));
-  VIE_TRY(w.alloc(sizeof(double2) * 3 * N));
+  // device staging buffers: allocated by the first call, kept by the plan
+  DevBuf &eps = P->h_eps, &e = P->h_e, &w = P->h_w;
+  if (!eps.p) VIE_TRY(eps.alloc(sizeof(double2) * N));
+  if (!e.p) VIE_TRY(e.alloc(sizeof(double2) * 3 * N));
+  if (!w.p) VIE_TRY(w.alloc(sizeof(double2) * 3 * N));
   VIE_CUDA(cudaMemcpyAsync(eps.p, eps_host, sizeof(double2) * N, cudaMemcpyHostToDevice, P->st));
   VIE_CUDA(cudaMemcpyAsync(e.p, e_inc_host, sizeof(double2) * 3 * N, cudaMemcpyHostToDevice, P->st));
   VIE_TRY(vie_set_permittivity(P, eps.p));
@@ -409,22 +410,27 @@ vie_status vie_solve_host(vie_plan_t P, const void* eps_host, const void* e_inc_
 
 vie_status vie_solve_batch(vie_plan_t* plans, int n, const void* const* e_inc, void* const* w_out, vie_info* info) {
   if (n < 0 || (n > 0 && (!plans || !e_inc || !w_out))) { set_error("vie_solve_batch: bad arguments"); return VIE_EINVAL; }
-  std::vector<vie_status> st(n, VIE_OK);
-  std::vector<std::string> errs(n);
-  std::vector<std::thread> th;
+  if (n == 0) return VIE_OK;
+  int dev = 0;
+  VIE_CUDA(cudaGetDevice(&dev));
   for (int i = 0; i < n; ++i) {
-    th.emplace_back([&, i] {
-      cudaSetDevice(plans[i]->device);
-      st[i] = vie_solve(plans[i], e_inc[i], w_out[i], info ? info + i : nullptr);
-      if (st[i] < 0) errs[i] = vie_last_error();
-    });
+    if (!plans[i] || !e_inc[i] || !w_out[i]) { set_error("vie_solve_batch: NULL plan or vector %d", i); return VIE_EINVAL; }
+    if (plans[i]->device != dev) { set_error("vie_solve_batch: plan %d belongs to another device", i); return VIE_EINVAL; }
+    for (int k = 0; k < i; ++k)
+      if (plans[k] == plans[i]) { set_error("vie_solve_batch: plan %d appears twice", i); return VIE_EINVAL; }
   }
-  for (auto& t : th) t.join();
-  vie_status worst = VIE_OK;
-  for (int i = 0; i < n; ++i) {
-    if (st[i] < 0 && (worst >= 0 || st[i] < worst)) { worst = st[i]; set_error("%s", errs[i].c_str()); }
-    else if (worst == VIE_OK && st[i] > 0) worst = st[i];
+  cudaStream_t st;
+  VIE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  std::vector<vie_status> status(n, VIE_OK);
+  vie_status worst;
+  {
+    StreamScope scope(st);
+    worst = solve_many(reinterpret_cast<vie_plan_s* const*>(plans), n,
+                       reinterpret_cast<const double2* const*>(e_inc), reinterpret_cast<double2* const*>(w_out), info,
+                       status.data(), st);
   }
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
   return worst;
 }
 
@@ -439,7 +445,8 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
   const double Sx = (3.0 * L * 16 > 200 * 1024) ? 3.0 * Pz * Py * L * (16 + 8) : 0;
   const double Xs = (L > 12736) ? 3.0 * Pz * Py * L * 16 + L * Py * Pz * 16 : 0;   // long-line split scratch
   const double vec = N * 3 * (16 * 6 + 8 * 8) + N * 24;
-  const int R = o.restart;
+  const int R = o.precision == VIE_MIXED ? (o.inner_restart > 0 ? o.inner_restart : std::min(2 * o.restart, 128))
+                                         : o.restart;
   const double basis = N * 3 * (R + 1) * (o.precision == VIE_MIXED ? 8 : 16);
   double prec = 0;
   if (o.precond == VIE_PREC_CIRCULANT) {
@@ -468,6 +475,18 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
 
 // ---------------------------------------------------------------------------
 // continuous-batching server
+//
+// Requests wait in a FIFO queue until their estimated device footprint fits
+// the budget and fewer than max_inflight are admitted.  Preparation workers
+// (threads) each take an admitted request: plan creation on the request's
+// own stream, the upload of its permittivity and incident field, the
+// preconditioner build and the start of its solve.  One driver thread keeps
+// every prepared request in a lockstep set: each pass runs a chunk of Arnoldi
+// steps of all of them as one step graph (the step kernels as single launches
+// over the work-list of the set), and requests join the set between passes
+// as they become ready and leave it as they finish, so the batch on the GPU
+// changes continuously.  A finished request's result is copied to its host
+// buffer, its plan released, and its status published.
 // ---------------------------------------------------------------------------
 struct SrvReq {
   int64_t id;
@@ -481,6 +500,11 @@ struct SrvReq {
   vie_status status = VIE_PENDING;
   vie_info info{};
   std::string err;
+  // while admitted (owned by one thread at a time: worker, then driver)
+  cudaStream_t st = nullptr;
+  vie_plan_t plan = nullptr;
+  vie::Run* run = nullptr;
+  vie_info run_info{};
 };
 
 struct vie_server_s {
@@ -488,54 +512,171 @@ struct vie_server_s {
   int max_inflight = 1;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<SrvReq*> queue;
+  std::condition_variable cv_work, cv_done, cv_ready;
+  std::deque<SrvReq*> queue;              // submitted, not admitted
+  std::deque<SrvReq*> ready;              // prepared, waiting to join the lockstep set
   std::map<int64_t, std::unique_ptr<SrvReq>> all;
   size_t reserved = 0;
-  int running = 0;
+  int running = 0;                        // admitted and not finished
   int64_t next_id = 1;
   bool stop = false;
   std::vector<std::thread> workers;
+  std::thread driver;
 };
 
-static void server_run_one(vie_server_s* S, SrvReq* R, cudaStream_t st) {
-  vie_plan_t plan = nullptr;
-  vie_status s = vie_plan_create(R->nx, R->ny, R->nz, R->h, R->k0, R->eps_bg, &R->opts, st, &plan);
-  if (s >= 0) s = vie_solve_host(plan, R->eps.data(), R->e.data(), R->w_out, &R->info);
-  if (s < 0) R->err = vie_last_error();
-  vie_plan_destroy(plan);
-  R->status = s;
+// release an admitted request's resources (on the thread that owns it)
+static void server_release(SrvReq* R) {
+  if (R->run) vie::run_delete(R->run);
+  R->run = nullptr;
+  if (R->plan) vie_plan_destroy(R->plan);
+  R->plan = nullptr;
+  if (R->st) cudaStreamDestroy(R->st);
+  R->st = nullptr;
+}
+
+// publish a finished request (status last, under the mutex: a poller that
+// sees it also sees info, the result and the error text)
+static void server_publish(vie_server_s* S, SrvReq* R, vie_status st, const vie_info& info, const std::string& err) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    R->info = info;
+    R->err = err;
+    R->status = st;
+    R->eps.clear(); R->eps.shrink_to_fit();
+    R->e.clear(); R->e.shrink_to_fit();
+    S->reserved -= R->est;
+    S->running -= 1;
+  }
+  S->cv_work.notify_all();
+  S->cv_done.notify_all();
+}
+
+// preparation: plan, inputs, preconditioner, start of the solve
+static vie_status server_prepare(SrvReq* R) {
+  VIE_CUDA(cudaStreamCreateWithFlags(&R->st, cudaStreamNonBlocking));
+  VIE_TRY(vie_plan_create(R->nx, R->ny, R->nz, R->h, R->k0, R->eps_bg, &R->opts, R->st, &R->plan));
+  vie_plan_s* P = R->plan;
+  StreamScope scope(P->st);
+  const long long N = (long long)P->nx * P->ny * P->nz;
+  VIE_TRY(P->h_eps.alloc(sizeof(double2) * N));
+  VIE_TRY(P->h_e.alloc(sizeof(double2) * 3 * N));
+  VIE_TRY(P->h_w.alloc(sizeof(double2) * 3 * N));
+  VIE_CUDA(cudaMemcpyAsync(P->h_eps.p, R->eps.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, P->st));
+  VIE_CUDA(cudaMemcpyAsync(P->h_e.p, R->e.data(), sizeof(double2) * 3 * N, cudaMemcpyHostToDevice, P->st));
+  VIE_TRY(vie_set_permittivity(P, P->h_eps.p));
+  VIE_CUDA(cudaStreamSynchronize(P->st));   // host copies of the inputs may go
+  R->run = vie::run_new(P, P->h_e.as<double2>(), P->h_w.as<double2>(), &R->run_info);
+  return vie::run_start(R->run);
 }
 
 static void server_worker(vie_server_s* S) {
   cudaSetDevice(S->device);
-  cudaStream_t st;
-  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
     SrvReq* R = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       // admit the oldest request once its footprint fits the budget
       S->cv_work.wait(lk, [&] {
-        return S->stop || (!S->queue.empty() && S->reserved + S->queue.front()->est <= S->budget);
+        return S->stop || (!S->queue.empty() && S->running < S->max_inflight &&
+                           S->reserved + S->queue.front()->est <= S->budget);
       });
-      if (S->stop && S->queue.empty()) break;
       if (S->stop) break;
       R = S->queue.front();
       S->queue.pop_front();
       S->reserved += R->est;
       S->running += 1;
     }
-    server_run_one(S, R, st);
+    const vie_status s = server_prepare(R);
+    if (s < 0 || vie::run_finished(R->run)) {
+      // failed, or finished at once (a zero right-hand side)
+      std::string err = s < 0 ? std::string(vie_last_error()) : std::string();
+      vie_status st = s;
+      if (s >= 0) {
+        st = vie::run_status(R->run, &err);
+        if (st >= 0 && cudaMemcpy(R->w_out, R->plan->h_w.p, sizeof(double2) * 3 * (size_t)R->nx * R->ny * R->nz,
+                                  cudaMemcpyDeviceToHost) != cudaSuccess) {
+          st = VIE_ECUDA;
+          err = "vie_server: result copy failed";
+        }
+      } else if (R->run) {
+        vie::run_status(R->run, &err);
+      }
+      const vie_info info = R->run_info;
+      server_release(R);
+      server_publish(S, R, st, info, err);
+      continue;
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->reserved -= R->est;
-      S->running -= 1;
-      R->eps.clear(); R->eps.shrink_to_fit();
-      R->e.clear(); R->e.shrink_to_fit();
+      S->ready.push_back(R);
     }
-    S->cv_work.notify_all();
-    S->cv_done.notify_all();
+    S->cv_ready.notify_all();
+  }
+}
+
+static void server_driver(vie_server_s* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  vie::Lockstep* L = nullptr;
+  {
+    StreamScope scope(st);
+    L = vie::lockstep_new();
+  }
+  std::vector<SrvReq*> active;
+  std::vector<vie::Run*> runs;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (active.empty()) S->cv_ready.wait(lk, [&] { return S->stop || !S->ready.empty(); });
+      if (S->stop) break;
+      while (!S->ready.empty()) {   // requests join the set between passes
+        active.push_back(S->ready.front());
+        S->ready.pop_front();
+      }
+    }
+    runs.clear();
+    for (SrvReq* R : active) runs.push_back(R->run);
+    bool stepped;
+    {
+      StreamScope scope(st);
+      stepped = vie::lockstep_pass(L, runs, st);
+    }
+    if (!stepped) {
+      // every run of the set is either in a cycle or finished; a run in
+      // neither state would never progress: fail it rather than spin
+      for (SrvReq* R : active)
+        if (!vie::run_finished(R->run)) vie::run_abort(R->run, "vie_server: request lost its GMRES cycle");
+    }
+    // requests that finished leave the set
+    for (size_t i = 0; i < active.size();) {
+      SrvReq* R = active[i];
+      if (!vie::run_finished(R->run)) { ++i; continue; }
+      std::string err;
+      vie_status s = vie::run_status(R->run, &err);
+      if (s >= 0) {
+        vie_plan_s* P = R->plan;
+        if (cudaMemcpyAsync(R->w_out, P->h_w.p, sizeof(double2) * 3 * (size_t)P->nx * P->ny * P->nz,
+                            cudaMemcpyDeviceToHost, P->st) != cudaSuccess ||
+            cudaStreamSynchronize(P->st) != cudaSuccess) {
+          s = VIE_ECUDA;
+          err = "vie_server: result copy failed";
+        }
+      }
+      const vie_info info = R->run_info;
+      server_release(R);
+      server_publish(S, R, s, info, err);
+      active.erase(active.begin() + i);
+    }
+  }
+  for (SrvReq* R : active) {
+    server_release(R);
+    server_publish(S, R, VIE_EREJECTED, vie_info{}, "server destroyed");
+  }
+  {
+    StreamScope scope(st);
+    vie::lockstep_release(L);
+    vie::lockstep_free(L);
   }
   cudaStreamDestroy(st);
 }
@@ -543,7 +684,7 @@ static void server_worker(vie_server_s* S) {
 extern "C" {
 
 vie_status vie_server_create(size_t budget_bytes, int max_inflight, vie_server_t* out) {
-  if (!out || budget_bytes == 0 || max_inflight < 1 || max_inflight > 64) {
+  if (!out || budget_bytes == 0 || max_inflight < 1 || max_inflight > 256) {
     set_error("vie_server_create: bad arguments");
     return VIE_EINVAL;
   }
@@ -552,7 +693,9 @@ vie_status vie_server_create(size_t budget_bytes, int max_inflight, vie_server_t
   S->budget = budget_bytes;
   S->max_inflight = max_inflight;
   cudaGetDevice(&S->device);
-  for (int i = 0; i < max_inflight; ++i) S->workers.emplace_back(server_worker, S);
+  // preparation workers: up to four plans built at once beside the solves
+  for (int i = 0; i < std::min(max_inflight, 4); ++i) S->workers.emplace_back(server_worker, S);
+  S->driver = std::thread(server_driver, S);
   *out = S;
   return VIE_OK;
 }
@@ -630,7 +773,15 @@ void vie_server_destroy(vie_server_t S) {
     S->queue.clear();
   }
   S->cv_work.notify_all();
+  S->cv_ready.notify_all();
   for (auto& t : S->workers) t.join();
+  S->driver.join();
+  // prepared requests that never joined the set
+  for (SrvReq* R : S->ready) {
+    server_release(R);
+    R->status = VIE_EREJECTED;
+    R->err = "server destroyed";
+  }
   delete S;
 }
 

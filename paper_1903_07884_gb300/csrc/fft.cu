@@ -17,8 +17,13 @@
 namespace vie {
 
 static std::atomic<long long> g_launches{0};
-void count_launch(int n) { g_launches += n; }
+static thread_local long long t_launches = 0;   // this thread's share (graph capture accounting)
+void count_launch(int n) {
+  g_launches += n;
+  t_launches += n;
+}
 long long launches_total() { return g_launches.load(); }
+long long launches_thread() { return t_launches; }
 
 bool fft_smooth(int n) {
   if (n < 1) return false;
@@ -39,18 +44,27 @@ static int next_pow2(int n) {
   return m;
 }
 
-// radix sequence: 8s, then one 4 or 2, then 3s, 5s, 7s
-static bool factorize(int n, FftPlanDev& p) {
+// radix sequence: 8s, then one 4 or 2, then 3s, 5s, 7s (the order the fused
+// x pass and the line kernels assume); false if n is not 7-smooth or needs
+// more than FFT_MAX_PASSES passes
+bool fft_factorize(int n, FftPlanDev& p) {
   p.n = n;
   p.npass = 0;
   int m = n, a = 0;
   while (m % 2 == 0) { m /= 2; ++a; }
-  while (a >= 3) { p.radix[p.npass++] = 8; a -= 3; }
-  if (a == 2) p.radix[p.npass++] = 4;
-  if (a == 1) p.radix[p.npass++] = 2;
+  auto push = [&p](int r) {
+    if (p.npass >= FFT_MAX_PASSES) return false;
+    p.radix[p.npass++] = r;
+    return true;
+  };
+  for (; a >= 3; a -= 3)
+    if (!push(8)) return false;
+  if (a == 2 && !push(4)) return false;
+  if (a == 1 && !push(2)) return false;
   for (int r : {3, 5, 7})
-    while (m % r == 0) { p.radix[p.npass++] = r; m /= r; if (p.npass >= FFT_MAX_PASSES) return false; }
-  return m == 1 && p.npass <= FFT_MAX_PASSES;
+    for (; m % r == 0; m /= r)
+      if (!push(r)) return false;
+  return m == 1;
 }
 
 template <class C>
@@ -64,7 +78,7 @@ static vie_status upload(const std::vector<std::complex<double>>& v, C** out) {
 }
 
 static vie_status make_plan(int n, FftPlanDev& p64, FftPlanDev& p32) {
-  if (!factorize(n, p64)) { set_error("fft: %d is not 7-smooth", n); return VIE_EINVAL; }
+  if (!fft_factorize(n, p64)) { set_error("fft: %d is not 7-smooth", n); return VIE_EINVAL; }
   fft_plan_finalize(p64);
   p32 = p64;
   std::vector<std::complex<double>> tw(n);

@@ -361,6 +361,10 @@ __device__ __forceinline__ C* fft_smem_pp(C* a, C* b, const FftPlanDev& p, const
 bool fft_smooth(int n);
 // Smallest 7-smooth integer >= n.
 int fft_next_smooth(int n);
+// Radix sequence of a 7-smooth length (fills p.n, p.npass, p.radix; the
+// caller runs fft_plan_finalize); false if n is not 7-smooth or needs more
+// than FFT_MAX_PASSES passes.
+bool fft_factorize(int n, FftPlanDev& p);
 
 // One transform length with its twiddle tables (or a Bluestein chirp-z
 // decomposition through a smooth length M >= 2n - 1 when n is not smooth).

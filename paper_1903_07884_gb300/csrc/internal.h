@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <memory>
+#include <string>
 #include <vector>
 
 #include "fft.cuh"
@@ -24,6 +25,16 @@ struct DevBuf {
   void release();
   vie_status alloc(size_t n);
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Stream of this thread's stream-ordered allocations (DevBuf::alloc) and a
+// scope that sets it; buffers are freed on the stream they were allocated on.
+cudaStream_t alloc_stream();
+void set_alloc_stream(cudaStream_t s);
+struct AllocScope {
+  cudaStream_t prev;
+  explicit AllocScope(cudaStream_t s) : prev(alloc_stream()) { set_alloc_stream(s); }
+  ~AllocScope() { set_alloc_stream(prev); }
 };
 
 // Matvec geometry passed to kernels.
@@ -91,6 +102,7 @@ struct vie_plan_s {
   vie::DevBuf U128, U64;               // [3][nz][Py][nx] y-spectrum of the unpadded z rows (yz_split)
   vie::DevBuf xin64, xout64;           // c64 staging for vie_matvec / precond (mixed)
   vie::DevBuf dev_err;                 // int: set by a kernel whose bounded wait ran out
+  vie::DevBuf h_eps, h_e, h_w;         // device staging of vie_solve_host (first call allocates)
   bool has_eps = false;
   bool prec_built = false;
   std::vector<std::unique_ptr<vie::BoxPrec>> bp;
@@ -107,6 +119,7 @@ struct vie_plan_s {
 namespace vie {
 
 long long launches_total();
+long long launches_thread();   // launches counted by the calling thread
 
 // greens.cu
 vie_status build_spectra(vie_plan_s* P);
@@ -133,8 +146,24 @@ vie_status apply_box2(vie_plan_s* P, BoxPrec& B, const C* r, C* z, C* inv, C* rh
 
 // krylov.cu
 vie_status solve(vie_plan_s* P, const double2* e_inc, double2* w, vie_info* info);
+vie_status solve_many(vie_plan_s* const* P, int n, const double2* const* e_inc, double2* const* w_out,
+                      vie_info* info, vie_status* status, cudaStream_t st);
 void krylov_free(vie_plan_s* P);
 void reset_graphs(vie_plan_s* P);
+// resumable solves ("runs") and the lockstep driver, for the server
+struct Run;
+struct Lockstep;
+Run* run_new(vie_plan_s* P, const double2* e_inc, double2* w_out, vie_info* info);
+void run_delete(Run* R);
+vie_status run_start(Run* R);          // right-hand side, preconditioner, first cycle (plan stream)
+bool run_finished(const Run* R);
+void run_abort(Run* R, const char* why);   // mark a run failed
+vie_status run_status(const Run* R, std::string* err);
+vie_plan_s* run_plan(const Run* R);
+Lockstep* lockstep_new();
+void lockstep_free(Lockstep* L);
+void lockstep_release(Lockstep* L);    // frees its device buffers, streams and graph
+bool lockstep_pass(Lockstep* L, std::vector<Run*>& runs, cudaStream_t st);
 
 // conversions
 vie_status widen(const float2* a, double2* b, long long n, cudaStream_t st);

@@ -21,7 +21,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "internal.h"
 
@@ -36,27 +35,19 @@ constexpr size_t kStaticScratchBytes = 64ull << 20;   // 64 MiB
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch for each device, resolved once with that
-// device current (host code may not use the symbol itself as a pointer).
-static std::mutex g_static_mu;
-static void* g_static_ptr[64] = {nullptr};
-
+// Device address of g_static_scratch on the current device.  Host code may
+// not use the symbol itself as a pointer, and the address can change when a
+// device's context is re-created (cudaDeviceReset), so it is looked up on
+// every call (a host-side query that allocates nothing).
 static vie_status static_scratch(void** out) {
-  int dev = 0;
-  VIE_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) { set_error("vie_matvec_static: device index %d out of range", dev); return VIE_EINVAL; }
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      set_error("vie_matvec_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return VIE_ECUDA;
-    }
-    g_static_ptr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    set_error("vie_matvec_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return VIE_ECUDA;
   }
-  *out = g_static_ptr[dev];
+  *out = p;
   return VIE_OK;
 }
 
@@ -70,22 +61,15 @@ __global__ void k_twiddles(double2* __restrict__ tw, int n) {
 }
 
 static bool factor_radices(int n, FftPlanDev& p) {
-  p.n = n;
-  p.npass = 0;
-  int m = n, a = 0;
-  while (m % 2 == 0) { m /= 2; ++a; }
-  while (a >= 3) { p.radix[p.npass++] = 8; a -= 3; }
-  if (a == 2) p.radix[p.npass++] = 4;
-  if (a == 1) p.radix[p.npass++] = 2;
-  for (int r : {3, 5, 7})
-    while (m % r == 0) {
-      if (p.npass >= FFT_MAX_PASSES) return false;
-      p.radix[p.npass++] = r;
-      m /= r;
-    }
-  if (m != 1) return false;
+  if (!fft_factorize(n, p)) return false;
   fft_plan_finalize(p);
   return true;
+}
+
+// true if the byte ranges [a, a + na) and [b, b + nb) share a byte
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
 }
 
 struct Carve {
@@ -124,10 +108,18 @@ using namespace vie;
 
 extern "C" vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double eps_bg,
                                         const void* eps_dev, const void* x_dev, void* y_dev, void* cuda_stream) {
-  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0) || !(k0 >= 0) || !(eps_bg > 0) || !eps_dev || !x_dev || !y_dev ||
-      x_dev == y_dev) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0) || !(k0 >= 0) || !(eps_bg > 0) || !eps_dev || !x_dev || !y_dev) {
     set_error("vie_matvec_static: invalid arguments");
     return VIE_EINVAL;
+  }
+  {
+    // y is written while x and eps are still read: no byte of y may alias them
+    const size_t nvox = (size_t)nx * ny * nz;
+    if (overlaps(x_dev, 3 * nvox * sizeof(double2), y_dev, 3 * nvox * sizeof(double2)) ||
+        overlaps(eps_dev, nvox * sizeof(double2), y_dev, 3 * nvox * sizeof(double2))) {
+      set_error("vie_matvec_static: y overlaps x or eps");
+      return VIE_EINVAL;
+    }
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   vie_plan_s P;   // geometry only: owns no device memory

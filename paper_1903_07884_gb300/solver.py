@@ -27,10 +27,10 @@ def to_device(a: np.ndarray, device="cuda"):
 
 def make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_CIRCULANT, homog=vie.VIE_HOM_REALMEAN,
               reduce_tol=1e-3, tol=1e-9, restart=50, max_iter=5000, inner_tol=1e-6, max_refine=1000,
-              boxes: Optional[Sequence] = None) -> vie.vie_opts:
+              boxes: Optional[Sequence] = None, inner_restart=0) -> vie.vie_opts:
     return vie.default_opts(precision=precision, precond=precond, homog=homog, reduce_tol=reduce_tol, tol=tol,
                             restart=restart, max_iter=max_iter, inner_tol=inner_tol, max_refine=max_refine,
-                            boxes=list(boxes) if boxes else None)
+                            boxes=list(boxes) if boxes else None, inner_restart=inner_restart)
 
 
 class Plan:

@@ -32,7 +32,7 @@ class vie_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("homog", ctypes.c_int),
                 ("reduce_tol", ctypes.c_double), ("boxes", ctypes.POINTER(vie_box)),
-                ("nboxes", ctypes.c_int)]
+                ("nboxes", ctypes.c_int), ("inner_restart", ctypes.c_int)]
 
 
 class vie_info(ctypes.Structure):

@@ -1,6 +1,8 @@
-"""Batched solves and the continuous-batching server (GPU): every result is
-the same alone and in the mix, admission never exceeds the device budget,
-oversized requests are rejected, and a poisoned request fails alone."""
+"""Batched solves and the continuous-batching server (GPU): every result
+matches the CPU oracle's solution of its system (oracle GMRES to 1e-12,
+relative error <= 1e-6) and is the same alone and in the mix, admission never
+exceeds the device budget, oversized requests are rejected, and a poisoned
+request fails alone."""
 import ctypes
 import threading
 import time
@@ -9,6 +11,7 @@ import numpy as np
 import pytest
 
 from gpu_common import cuda_or_fail, relerr
+from oracle import solve as osolve
 from paper_1903_07884_gb300 import inputs, vie
 from paper_1903_07884_gb300.solver import Plan, make_opts, to_device
 
@@ -20,6 +23,18 @@ def _problems():
             inputs.bragg_grating(128, 12, 4, 0.025, 1.50, wide=8, narrow=6, period=16, name="b"),
             inputs.directional_coupler(80, 0.025, 1.58, ny=24, nz=4, core_w=8, gap=4, margin=2, name="c"),
             inputs.straight_guide(131, 8, 4, 0.025, 1.52, core_ny=6, core_nz=4, name="d")]
+
+
+_ORACLE = {}
+
+
+def _oracle_solution(p):
+    """The oracle's solution of a request's system, cached per problem name."""
+    if p.name not in _ORACLE:
+        s = osolve.iterative_solve(p, tol=1e-12, tau=1e-3, max_iter=20000)
+        assert s.relres <= 1e-12, (p.name, s.relres)
+        _ORACLE[p.name] = s.w
+    return _ORACLE[p.name]
 
 
 def _opts(p, precision=vie.VIE_MIXED):
@@ -53,6 +68,46 @@ def test_batch_equals_individual_solves():
     for i, p in enumerate(probs):
         assert infos[i].relres <= 1e-9
         np.testing.assert_array_equal(ws[i].cpu().numpy(), alone[i])
+        assert relerr(alone[i], _oracle_solution(p)) <= 1e-6, p.name
+    for pl in plans:
+        pl.close()
+
+
+def test_batch_mixes_precisions_and_uneven_lengths():
+    """One lockstep batch of plans of different lengths (nx 96, 131, 200),
+    cross-sections and precisions (two complex-FP32 GMRES-IR solves and one
+    FP64 solve): the Arnoldi kernels of each step run as one launch over the
+    work-list of all plans of a precision, and every result is bitwise the
+    result of the same plan solved alone."""
+    torch = cuda_or_fail()
+    probs = [inputs.straight_guide(96, 8, 4, 0.05, 1.55, absorber=8, name="u0"),
+             inputs.straight_guide(131, 8, 4, 0.025, 1.52, core_ny=6, core_nz=4, name="u1"),
+             inputs.bragg_grating(200, 12, 4, 0.025, 1.50, wide=8, narrow=6, period=16, name="u2")]
+    precs = [vie.VIE_MIXED, vie.VIE_FP64, vie.VIE_MIXED]
+    alone = []
+    for p, pr in zip(probs, precs):
+        plan = Plan.for_problem(p, precision=pr)
+        plan.set_permittivity(p.eps)
+        w, info = plan.solve(p.e_inc)
+        alone.append(w.cpu().numpy())
+        plan.close()
+    plans, es, ws = [], [], []
+    for p, pr in zip(probs, precs):
+        pl = Plan.for_problem(p, precision=pr)
+        pl.set_permittivity(p.eps)
+        e = to_device(p.e_inc)
+        es.append(e)
+        ws.append(torch.empty_like(e))
+        plans.append(pl)
+    torch.cuda.synchronize()
+    launches0 = vie.vie_kernel_launches()
+    infos = vie.vie_solve_batch([pl.handle for pl in plans], [e.data_ptr() for e in es], [w.data_ptr() for w in ws])
+    torch.cuda.synchronize()
+    assert vie.vie_kernel_launches() > launches0
+    for i, p in enumerate(probs):
+        assert infos[i].relres <= 1e-9
+        np.testing.assert_array_equal(ws[i].cpu().numpy(), alone[i])
+        assert relerr(alone[i], _oracle_solution(p)) <= 1e-6, p.name
     for pl in plans:
         pl.close()
 
@@ -91,6 +146,7 @@ def test_server_results_alone_equal_results_in_the_mix():
             assert st == vie.VIE_OK
             res = _wait(srv, [t])
             assert res[t][0] == vie.VIE_OK, vie.last_error()
+            assert relerr(w, _oracle_solution(p)) <= 1e-6, p.name
             alone.append(w)
         # all at once, twice over, arriving while others run
         outs, tickets = [], []
@@ -212,3 +268,45 @@ def test_server_concurrent_medium_requests_bitwise():
     for i in range(len(probs)):
         assert done[i][0] == vie.VIE_OK, (i, done[i], vie.last_error())
         np.testing.assert_array_equal(bufs[i][2], alone[i])
+
+
+def test_server_twelve_requests_join_and_leave_the_lockstep_set():
+    """Twelve small requests of uneven lengths, both precisions, submitted in
+    two waves: the driver's lockstep set grows beyond eight runs and changes
+    as requests join and finish; every result is bitwise the solo result."""
+    cuda_or_fail()
+    probs, precs = [], []
+    for i in range(12):
+        nx = 40 + 13 * i
+        if i % 3 == 2:
+            probs.append(inputs.bragg_grating(nx, 12, 4, 0.025, 1.50 + 0.005 * i, wide=8, narrow=6, period=16,
+                                              name=f"t{i}"))
+        else:
+            probs.append(inputs.straight_guide(nx, 8, 4, 0.05, 1.50 + 0.005 * i, absorber=4, name=f"t{i}"))
+        precs.append(vie.VIE_FP64 if i % 4 == 3 else vie.VIE_MIXED)
+    alone = []
+    for p, pr in zip(probs, precs):
+        plan = Plan.for_problem(p, precision=pr)
+        plan.set_permittivity(p.eps)
+        w, info = plan.solve(p.e_inc)
+        alone.append(w.cpu().numpy())
+        plan.close()
+    srv = vie.vie_server_create(64 << 30, 12)
+    outs, tickets = [], []
+    try:
+        for wave in (range(0, 7), range(7, 12)):
+            for i in wave:
+                p = probs[i]
+                w = np.empty(p.e_inc.shape, dtype=np.complex128)
+                st, t = _submit(srv, p, w, _opts(p, precs[i]))
+                assert st == vie.VIE_OK
+                outs.append(w)
+                tickets.append(t)
+            time.sleep(0.05)
+        res = _wait(srv, tickets, timeout=300)
+    finally:
+        vie.vie_server_destroy(srv)
+    assert len(res) == len(tickets)
+    for i, t in enumerate(tickets):
+        assert res[t][0] == vie.VIE_OK, (i, res[t])
+        np.testing.assert_array_equal(outs[i], alone[i])

@@ -54,3 +54,46 @@ def test_static_matvec_rejects_grids_beyond_its_scratch():
     st = vie.vie_matvec_static(nx, ny, nz, 0.025, K0, 1.0, eps.data_ptr(), x.data_ptr(), y.data_ptr(), 0)
     assert st == vie.VIE_EINVAL
     assert "scratch" in vie.last_error()
+
+
+def test_static_matvec_allocates_no_device_memory():
+    """The entry point's defining property: after one warm-up call (which
+    loads the library's device code under lazy loading), further calls --
+    including one on a grid with transform lengths not seen before -- leave
+    the device's free memory unchanged.  Inputs are allocated first."""
+    torch = cuda_or_fail()
+    shapes = [(24, 4, 2), (30, 4, 2)]      # same kernel variants, new embedding lengths L = 48, 60
+    bufs = []
+    for nx, ny, nz in shapes:
+        eps = to_device(inputs.random_permittivity(nz, ny, nx, seed=3))
+        x = to_device(inputs.random_field((3, nz, ny, nx), seed=4))
+        bufs.append((nx, ny, nz, eps, x, torch.empty_like(x)))
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call(i):
+        nx, ny, nz, eps, x, y = bufs[i]
+        st = vie.vie_matvec_static(nx, ny, nz, 0.05, K0, 1.0, eps.data_ptr(), x.data_ptr(), y.data_ptr(), stream)
+        assert st == vie.VIE_OK, vie.last_error()
+
+    call(0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    call(0)
+    call(1)
+    call(1)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_static_matvec_rejects_overlapping_output():
+    torch = cuda_or_fail()
+    nx, ny, nz = 8, 4, 2
+    n3 = 3 * nx * ny * nz
+    eps = to_device(inputs.random_permittivity(nz, ny, nx, seed=5))
+    buf = torch.zeros(2 * n3, dtype=torch.complex128, device="cuda")
+    x = buf[:n3]
+    y_partial = buf[n3 // 2:n3 // 2 + n3]          # shares half of x
+    st = vie.vie_matvec_static(nx, ny, nz, 0.05, K0, 1.0, eps.data_ptr(), x.data_ptr(), y_partial.data_ptr(), 0)
+    assert st == vie.VIE_EINVAL
+    assert "overlap" in vie.last_error()
