@@ -51,6 +51,8 @@ def workload(name):
         return inputs.workload_bragg(), "bragg_4096x24x8_2boxes"
     if name == "coupler":
         return inputs.workload_coupler(), "coupler_2048x48x8_2boxes"
+    if name == "coupler_batch":      # the batch's first wavelength (the batch itself runs in run_batch)
+        return inputs.workload_coupler(wavelength=1.50), "coupler_2048x48x8_2boxes_lambda1.50"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -148,10 +150,11 @@ def algorithmic(kernel: str, p, plan_meta: dict):
         return "hbm", c * (2 * T + oct_)
     if kernel == "mv_yz_inv_c64":
         return "hbm", c * (T + n3 + N + n3)
+    k = plan_meta.get("plans_per_launch", 1)     # the Arnoldi kernels cover every plan of a batch per launch
     if kernel == "arnoldi_dot_c64":       # reads w, u_j and V_0..V_{j-1}
-        return "hbm", c * (jbar + 2) * n3
+        return "hbm", k * c * (jbar + 2) * n3
     if kernel == "arnoldi_update_c64":    # reads the same, writes q_j and w''
-        return "hbm", c * (jbar + 4) * n3
+        return "hbm", k * c * (jbar + 4) * n3
     if kernel == "block_gemv_c64":
         m, nh = plan_meta["m"], plan_meta["nhalf"]
         return "hbm", c * nh * m * m
@@ -174,10 +177,7 @@ def algorithmic(kernel: str, p, plan_meta: dict):
 # columns), per launch for the others.  Cleared whenever a kernel changes.
 TRAFFIC = {
     "long_straight_1024x16x8": {
-        "arnoldi_dot_c64": ("per_column", 122.67e6 / 38),
-        "arnoldi_update_c64": ("per_column", 123.00e6 / 38),
         "mv_x_c64": ("per_launch", 20.23e6),
-        "block_gemv_c64": ("per_launch", 132.71e6),
     }
 }
 
@@ -520,6 +520,7 @@ def run_gpu(args):
             "e2e": {"value": solves_per_s(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": int(16 * N + 16 * 3 * N), "d2h_bytes_per_step": int(16 * 3 * N)},
             "roofline": roof,
+            "autotune": vie.vie_plan_tuning(plan.handle),
             "matvec": matvec_summary(table, p, pk["hbm_gbs"]),
             "profile_ms": {k: round(v[1], 4) for k, v in top[:12]}}
     plan.close()
@@ -637,6 +638,173 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
         out["max_rel_err_vs_fp64"] = max(errs) if errs else None
         out["rel_err_vs_fp64_requests"] = len(errs)
     return out
+
+
+def run_batch(args):
+    """Directional-coupler batch (2048x48x8 grid, h = 0.025 um, two 16x8 Si
+    cores in SiO2 with one preconditioner box each): --batch-n wavelengths
+    spaced evenly over 1.50-1.60 um solved together through vie_solve_batch
+    (one lockstep set: per step one captured graph, the Arnoldi kernels as
+    single launches over the work-list of all plans), against the same
+    solves one after another.  One step = permittivity + preconditioner
+    build of every plan + the batch solve.  Prints one bench line."""
+    import numpy as np
+    import torch
+
+    from paper_1903_07884_gb300 import inputs, vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+
+    torch.cuda.set_device(0)
+    lams = inputs.coupler_wavelengths(args.batch_n)
+    probs = [inputs.workload_coupler(wavelength=float(l)) for l in lams]
+    p0 = probs[0]
+    plans = [Plan.for_problem(p, precision=vie.VIE_MIXED, tol=args.tol) for p in probs]
+    eps = [to_device(p.eps) for p in probs]
+    es = [to_device(p.e_inc) for p in probs]
+    ws = [torch.empty_like(e) for e in es]
+
+    def prepare():
+        for pl, e in zip(plans, eps):
+            pl.set_permittivity(e)
+            pl.build()
+
+    def batch_step():
+        prepare()
+        return vie.vie_solve_batch([pl.handle for pl in plans], [e.data_ptr() for e in es],
+                                   [w.data_ptr() for w in ws])
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        batch_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = vie.vie_kernel_launches()
+    times, infos = [], None
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = batch_step()      # synchronous: every plan's build and the batch solve are done on return
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = vie.vie_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    value = len(plans) * 1000.0 / ms
+    w_batch = [w.cpu().numpy() for w in ws]
+    # the same solves one after another
+    ts = []
+    seq_equal = True
+    for k in range(2):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        outs = []
+        for pl, e in zip(plans, eps):
+            pl.set_permittivity(e)
+            pl.build()
+        for pl, e in zip(plans, es):
+            w, _ = pl.solve(e)
+            outs.append(w)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        seq_equal = seq_equal and all(np.array_equal(o.cpu().numpy(), wb) for o, wb in zip(outs, w_batch))
+    ms_seq = statistics.mean(ts)
+    # per-kernel device time of one profiled batch step (eager launches)
+    vie.vie_profile_reset()
+    vie.vie_profile_enable(True)
+    batch_step()
+    torch.cuda.synchronize()
+    vie.vie_profile_enable(False)
+    table = vie.profile_table()
+    vie.vie_profile_reset()
+    total_prof = sum(t for _, t in table.values())
+    top = sorted(table.items(), key=lambda kv: -kv[1][1])
+    pk, pk_src = peaks()
+    meta = plan_meta(p0, infos[0].as_dict())
+    meta["plans_per_launch"] = len(plans)
+    roof = None
+    for name, (cnt, tot) in top:
+        a = algorithmic(name, p0, meta)
+        if a is None or a[0] != "hbm":
+            continue
+        avg_ms = tot / cnt
+        ach = a[1] / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "share": tot / total_prof, "avg_launch_ms": avg_ms,
+                "launches": cnt, "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)"}
+        break
+    # accuracy: each solution's FP64 residual recomputed by the CPU oracle on a
+    # sample of wavelengths, and the first one against the stored oracle sample
+    acc = {"relres_fp64_max": max(i.relres for i in infos)}
+    if not args.no_cpu_baseline:
+        chk = sorted({0, len(plans) // 2, len(plans) - 1})
+        rr = {}
+        for i in chk:
+            S = OracleResidual(probs[i])
+            rr[f"{lams[i]:.4f}"] = S.residual(w_batch[i])
+        acc["oracle_relres_sampled"] = rr
+        ref = oracle_solution_sample(f"coupler_2048x48x8_2boxes_lambda{lams[0]:.2f}")
+        if ref is not None:
+            idx, wref = ref
+            wv = w_batch[0].ravel()[idx]
+            acc["lambda0_vs_oracle_sample"] = {"rel_err": float(np.linalg.norm(wv - wref) / np.linalg.norm(wref)),
+                                               "max_err": float(np.abs(wv - wref).max() / np.abs(wref).max()),
+                                               "entries": int(idx.size)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": f"coupler_batch_{len(plans)}x2048x48x8_2boxes", "grid": [p0.nx, p0.ny, p0.nz],
+                       "wavelengths_um": [round(float(l), 5) for l in lams], "tol": args.tol,
+                       "precision": "mixed: c64 GMRES in FP64 iterative refinement",
+                       "preconditioner": "block-diagonal 1-level Chan-Olkin, one box per core, tau=1e-3",
+                       "l2": "512 MB buffer written between timed steps (outside the step events)"},
+            "iters": [i.iters_inner for i in infos], "clocks": clk, "gpu_launches": int(launches),
+            "sequential": {"ms_per_step": ms_seq, "value": len(plans) * 1000.0 / ms_seq,
+                           "bitwise_equal_to_batch": bool(seq_equal)},
+            "accuracy": acc, "roofline": roof, "autotune": vie.vie_plan_tuning(plans[0].handle),
+            "profile_ms": {k: round(v[1], 4) for k, v in top[:12]}}
+    for pl in plans:
+        pl.close()
+    print(json.dumps(line))
+    return 0
+
+
+class OracleResidual:
+    """The CPU oracle's FP64 relative residual of a solution (FFT matvec)."""
+
+    def __init__(self, p):
+        from oracle import operator as op
+        self.k = op.background_k(p.k0, p.eps_bg)
+        self.M = op.material(p.eps, p.eps_bg)
+        self.b = op.rhs(p.eps, p.eps_bg, p.e_inc)
+        self.spec = op.generator_spectra(p.nx, p.ny, p.nz, p.h, self.k)
+
+    def residual(self, w) -> float:
+        import numpy as np
+        from oracle import operator as op
+        r = self.b - op.fft_matvec(w, self.M, self.spec)
+        return float(np.linalg.norm(r) / np.linalg.norm(self.b))
+
+
+def oracle_solution_sample(wname: str):
+    """(indices, values) of a stored sampled oracle solution, or None."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "oracle_solutions.json")
+    if not os.path.exists(path):
+        return None
+    meta = json.load(open(path)).get(wname)
+    if not meta or "sample" not in meta:
+        return None
+    d = np.load(os.path.join(ROOT, "tests", "golden", meta["file"]))
+    return d["idx"], d["w"]
 
 
 def plan_meta(p, info):
@@ -806,7 +974,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gvie", choices=["gvie", "reference"])
-    ap.add_argument("--workload", default="long_straight")
+    ap.add_argument("--workload", default="long_straight",
+                    help="long_straight (default), small_straight, bragg, coupler, or coupler_batch")
+    ap.add_argument("--batch-n", type=int, default=16, help="coupler_batch: number of wavelengths")
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -835,6 +1005,8 @@ def main():
         return run_precond2_case(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "coupler_batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -316,6 +316,7 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   VIE_TRY(fft_get(d.Pz, &P->fPz));
   VIE_TRY(build_spectra(P.get()));
   VIE_TRY(matvec_alloc(P.get()));
+  VIE_TRY(tune_matvec(P.get()));
   VIE_TRY(P->dev_err.alloc(sizeof(int)));
   VIE_CUDA(cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), P->st));
   *out = P.release();

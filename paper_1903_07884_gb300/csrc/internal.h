@@ -5,6 +5,7 @@
 
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "fft.cuh"
@@ -68,6 +69,7 @@ struct BoxPrec {
   DevBuf zhat64, zhat128;
   DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
   DevBuf bpack, apack;       // tensor-core operands of the representative-block product (packed tf32 hi/lo)
+  int gemv_split = 0;        // kept-block product: CTAs per block (0: the default rule; set by the autotuner)
   const FftLen* fx = nullptr;
   // 2-level boxes: blocks of m2 = 3 nz rows for f <= n/2, g <= ny/2, slot
   // g * nfs + f, inverses column-major in inv64 / inv128; rhat/zhat [m2][ny][n]
@@ -93,6 +95,13 @@ struct vie_plan_s {
   vie::MvDims d{};
   const vie::FftLen *fL = nullptr, *fPy = nullptr, *fPz = nullptr;
   bool fused_x128 = true, fused_x64 = true;   // fused x-pass fits shared memory
+  // x-pass variant per precision [c64, c128] chosen by the autotuner (-1:
+  // untuned, the default rule; 0: compile-time radix-16 kernel; k >= 1: the
+  // generic Stockham kernel with radix order xord[.][k - 1])
+  int xvar[2] = {-1, -1};
+  vie::FftPlanDev xord[2][3]{};
+  std::string tuning;                  // the autotuner's report (vie_plan_tuning)
+  size_t tuning_matvec = 0;            // length of its matvec part (the rest belongs to the last build)
   vie::DevBuf spec128, spec64;         // [6][Pzh][Pyh][Lh] scaled generator spectra
   vie::DevBuf M128, M64;               // [nz][ny][nx] material M
   vie::DevBuf T128, T64;               // [3][Pz][Py][nx] matvec intermediate
@@ -129,6 +138,16 @@ vie_status set_material(vie_plan_s* P, const double2* eps);
 template <class C>
 vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C* T, C* S, cudaStream_t st);
 vie_status matvec_alloc(vie_plan_s* P);
+template <class C>
+vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStream_t st);
+
+// tune.cu: per-shape choice among launch variants, by timing on the plan's
+// own buffers (cached per process and shape)
+using TuneKey = std::tuple<int, int, int, int, int>;   // kernel, precision, shape...
+bool tune_cache_get(const TuneKey& k, int* choice, std::string* report);
+void tune_cache_put(const TuneKey& k, int choice, const std::string& report);
+vie_status tune_matvec(vie_plan_s* P);
+bool autotune_enabled();
 
 // precond.cu
 vie_status precond_build(vie_plan_s* P);

@@ -430,13 +430,29 @@ __device__ __forceinline__ void arn_dot4(const C (&v)[4][KPT], const C (&xu)[KPT
   __syncwarp();
 }
 
+// columns top, top - 1, .., top - nt + 1 (nt <= 4), for the update's
+// descending sweep
+template <class C, int KPT>
+__device__ __forceinline__ void arn_load4r(C (&v)[4][KPT], const C* __restrict__ V, long long ld, long long start,
+                                           int top, int nt, int ct, int cnt) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const C* col = V + (long long)(top - t) * ld + start;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      const int e = ct + q * ARN_THREADS;
+      v[t][q] = (t < nt && e < cnt) ? col[e] : czero<C>();
+    }
+  }
+}
+
 // the update of four columns: as += s_i V_i, ac += c_i V_i
 template <class C, int KPT>
 __device__ __forceinline__ void arn_axpy4(const C (&v)[4][KPT], const C* sco, const C* cco, C (&as)[KPT],
-                                          C (&ac)[KPT], int i0, int nt) {
+                                          C (&ac)[KPT], int top, int nt) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const C hs = t < nt ? sco[i0 + t] : czero<C>(), hc = t < nt ? cco[i0 + t] : czero<C>();
+    const C hs = t < nt ? sco[top - t] : czero<C>(), hc = t < nt ? cco[top - t] : czero<C>();
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
       cfma(as[q], hs, v[t][q]);
@@ -748,7 +764,11 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
     const R ibr = (R)ib;
     const int ct = threadIdx.x;
     C* Vj = V + (long long)j * ld;
-    for (int sb = 0; sb < g.nsub; ++sb) {
+    // the sweep runs backwards (last sub-chunk, highest column first): the
+    // dot pass just read the basis forwards, so the columns it read last are
+    // the likeliest still in L2, and the next dot pass starts on the columns
+    // this pass reads last
+    for (int sb = g.nsub - 1; sb >= 0; --sb) {
       const long long start = g.c0 + (long long)sb * g.sc;
       const int cnt = min(g.sc, g.c1 - (int)start);
       C as[KPT], ac[KPT];
@@ -758,13 +778,13 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
         ac[q] = czero<C>();
       }
       C va[4][KPT], vb[4][KPT];
-      if (j > 0) arn_load4<C, KPT>(va, V, ld, start, 0, min(4, j), ct, cnt);
-      for (int i0 = 0; i0 < j; i0 += 8) {
-        const int n1 = min(4, j - i0 - 4), n2 = min(4, j - i0 - 8);
-        if (n1 > 0) arn_load4<C, KPT>(vb, V, ld, start, i0 + 4, n1, ct, cnt);
-        arn_axpy4<C, KPT>(va, sco, cco, as, ac, i0, min(4, j - i0));
-        if (n2 > 0) arn_load4<C, KPT>(va, V, ld, start, i0 + 8, n2, ct, cnt);
-        if (n1 > 0) arn_axpy4<C, KPT>(vb, sco, cco, as, ac, i0 + 4, n1);
+      if (j > 0) arn_load4r<C, KPT>(va, V, ld, start, j - 1, min(4, j), ct, cnt);
+      for (int v0 = 0; v0 < j; v0 += 8) {
+        const int n1 = min(4, j - v0 - 4), n2 = min(4, j - v0 - 8);
+        if (n1 > 0) arn_load4r<C, KPT>(vb, V, ld, start, j - 1 - (v0 + 4), n1, ct, cnt);
+        arn_axpy4<C, KPT>(va, sco, cco, as, ac, j - 1 - v0, min(4, j - v0));
+        if (n2 > 0) arn_load4r<C, KPT>(va, V, ld, start, j - 1 - (v0 + 8), n2, ct, cnt);
+        if (n1 > 0) arn_axpy4<C, KPT>(vb, sco, cco, as, ac, j - 1 - (v0 + 4), n1);
       }
       // w and u_j only now, so that their registers are free during the sweep
       C xw[KPT], xu[KPT];

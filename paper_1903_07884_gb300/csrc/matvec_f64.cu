@@ -4,4 +4,5 @@
 namespace vie {
 template vie_status matvec<double2>(vie_plan_s*, const double2*, double2*, const double2*, const double2*,
                                     double2*, double2*, cudaStream_t);
+template vie_status xpass<double2>(vie_plan_s*, const double2*, double2*, double2*, int, cudaStream_t);
 }  // namespace vie

@@ -238,7 +238,7 @@ __device__ __forceinline__ void dft_pow2(float2 (&v)[N]) {
 }
 
 template <int R1, int R2, int R3>
-__global__ void __launch_bounds__(R2 * R3, 4) k_mv_x16(float2* __restrict__ T, const float2* __restrict__ spec,
+__global__ void __launch_bounds__(R2 * R3, 512 / (R2 * R3)) k_mv_x16(float2* __restrict__ T, const float2* __restrict__ spec,
                                                     MvDims d, const float2* __restrict__ twL) {
   constexpr int L = R1 * R2 * R3, S1 = L / R1, S2 = S1 / R2, GPT = R1 / R3;
   constexpr int LP = L + L / 16;
@@ -615,52 +615,35 @@ static vie_status set_smem(K kern, size_t smem) {
     default: set_error("matvec: tile too large for one block"); return VIE_EINVAL; \
   }
 
+// The x pass alone (pass B of the matvec) in one of its variants: T holds
+// the yz-transformed field on entry and the inverse x-transformed product on
+// exit.  The autotuner times the variants with this entry.
 template <class C>
-vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C* T, C* S, cudaStream_t st) {
+vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStream_t st) {
   const MvDims& d = P->d;
   const int cap = 16;
-  // pass A
-  const int XG = pick_xg(d, sizeof(C));
-  const size_t smemA = 2 * (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
-  dim3 gA(ceil_div(d.nx, XG), 3);
-  const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
-  // register transforms for the power-of-two cross-sections that have an instantiation
-  const int yzr = sizeof(C) == 8 ? ((d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0) : 0;
-  const size_t smemR = (size_t)d.nz * YZ_XG * (d.Py + 1) * sizeof(float2);
-  const dim3 gR(ceil_div(d.nx, YZ_XG), 3);
-  C* U = (C*)(sizeof(C) == 16 ? P->U128.p : P->U64.p);
-  const long long pyx = (long long)d.Py * d.nx;
-  if (P->yz_split) {
-    // y-lines of every (b, z) row (stride nx), padded to Py, into U; then
-    // z-lines of every (b, ky, x) (stride Py nx), padded to Pz, into T
-    LineDesc dy{d.ny, d.Py, 3 * d.nz * d.nx, d.nx, 3 * d.nz, 1, (long long)d.ny * d.nx, 0, d.nx,
-                1, pyx, 0, d.nx};
-    VIE_TRY(fft_lines<C>(x, U, dy, *P->fPy, -1, 1.0, nullptr, st));
-    LineDesc dz{d.nz, d.Pz, (int)(3 * pyx), (int)pyx, 3, 1, d.nz * pyx, 0, pyx, 1, d.Pz * pyx, 0, pyx};
-    VIE_TRY(fft_lines<C>(U, T, dz, *P->fPz, -1, 1.0, nullptr, st));
-  } else if (yzr) {
-    Prof pf_("mv_yz_fwd_c64", st);
-    if (yzr == 1) k_mv_yz_fwd_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
-    else k_mv_yz_fwd_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
-  } else {
-    auto k = k_mv_yz_fwd<C>;
-    VIE_TRY(set_smem(k, smemA));
-    Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);
-    k<<<gA, 256, smemA, st>>>(x, T, d, py, pz, XG);
-  }
-  if (!P->yz_split) count_launch();
-  VIE_CHECK_LAUNCH();
-  // pass B
+  const FftPlanDev plan_of = planof<C>(*P->fL);
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
   if (fused) {
     const size_t tile = (size_t)3 * d.L * sizeof(C);
-    if (sizeof(C) == 8 && d.L == 2048) {
+    // variant 0 (or -1, untuned): the compile-time radix-16 kernel where one
+    // exists; k >= 1: the generic Stockham kernel with radix order k - 1
+    const bool ct = sizeof(C) == 8 && (d.L == 2048 || d.L == 4096) && variant <= 0;
+    const FftPlanDev pl = variant >= 1 ? P->xord[sizeof(C) == 8 ? 0 : 1][variant - 1] : plan_of;
+    if (ct && d.L == 2048) {
       // compile-time radix structure 16 x 16 x 8 (complex FP32)
       constexpr int L = 2048;
       const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);
       Prof pf_("mv_x_c64", st);
       VIE_TRY(set_smem(k_mv_x16<16, 16, 8>, smem));
       k_mv_x16<16, 16, 8><<<d.Py * d.Pz, 128, smem, st>>>((float2*)T, (const float2*)spec, d, (const float2*)pl.tw);
+    } else if (ct && d.L == 4096) {
+      // 16 x 16 x 16, 256 threads, two blocks per SM
+      constexpr int L = 4096;
+      const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);
+      Prof pf_("mv_x_c64", st);
+      VIE_TRY(set_smem(k_mv_x16<16, 16, 16>, smem));
+      k_mv_x16<16, 16, 16><<<d.Py * d.Pz, 256, smem, st>>>((float2*)T, (const float2*)spec, d, (const float2*)pl.tw);
     } else if (2 * tile <= 200 * 1024) {
       auto k = k_mv_x<C, 0>;
       VIE_TRY(set_smem(k, 2 * tile));
@@ -700,6 +683,46 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     LineDesc li = lines_flat(d.L, d.nx, nl, d.L, 1, d.nx, 1);
     VIE_TRY(fft_lines<C>(S, T, li, *P->fL, +1, 1.0, X, st));
   }
+  return VIE_OK;
+}
+
+template <class C>
+vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C* T, C* S, cudaStream_t st) {
+  const MvDims& d = P->d;
+  const int cap = 16;
+  // pass A
+  const int XG = pick_xg(d, sizeof(C));
+  const size_t smemA = 2 * (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
+  dim3 gA(ceil_div(d.nx, XG), 3);
+  const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
+  // register transforms for the power-of-two cross-sections that have an instantiation
+  const int yzr = sizeof(C) == 8 ? ((d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0) : 0;
+  const size_t smemR = (size_t)d.nz * YZ_XG * (d.Py + 1) * sizeof(float2);
+  const dim3 gR(ceil_div(d.nx, YZ_XG), 3);
+  C* U = (C*)(sizeof(C) == 16 ? P->U128.p : P->U64.p);
+  const long long pyx = (long long)d.Py * d.nx;
+  if (P->yz_split) {
+    // y-lines of every (b, z) row (stride nx), padded to Py, into U; then
+    // z-lines of every (b, ky, x) (stride Py nx), padded to Pz, into T
+    LineDesc dy{d.ny, d.Py, 3 * d.nz * d.nx, d.nx, 3 * d.nz, 1, (long long)d.ny * d.nx, 0, d.nx,
+                1, pyx, 0, d.nx};
+    VIE_TRY(fft_lines<C>(x, U, dy, *P->fPy, -1, 1.0, nullptr, st));
+    LineDesc dz{d.nz, d.Pz, (int)(3 * pyx), (int)pyx, 3, 1, d.nz * pyx, 0, pyx, 1, d.Pz * pyx, 0, pyx};
+    VIE_TRY(fft_lines<C>(U, T, dz, *P->fPz, -1, 1.0, nullptr, st));
+  } else if (yzr) {
+    Prof pf_("mv_yz_fwd_c64", st);
+    if (yzr == 1) k_mv_yz_fwd_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
+    else k_mv_yz_fwd_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
+  } else {
+    auto k = k_mv_yz_fwd<C>;
+    VIE_TRY(set_smem(k, smemA));
+    Prof pf_(sizeof(C) == 8 ? "mv_yz_fwd_c64" : "mv_yz_fwd_c128", st);
+    k<<<gA, 256, smemA, st>>>(x, T, d, py, pz, XG);
+  }
+  if (!P->yz_split) count_launch();
+  VIE_CHECK_LAUNCH();
+  // pass B
+  VIE_TRY(xpass<C>(P, spec, T, S, P->xvar[sizeof(C) == 8 ? 0 : 1], st));
   // pass C
   if (P->yz_split) {
     // inverse z-lines (keep z < nz) into U, inverse y-lines (keep y < ny) into

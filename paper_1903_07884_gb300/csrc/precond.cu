@@ -16,6 +16,7 @@
 // n - f share one block read.  Frequencies outside K use the central block
 // D_{ceil(n/2)} (1-based) through one multi-right-hand-side product.
 #include <math.h>
+#include <stdio.h>
 
 #include <algorithm>
 #include <chrono>
@@ -687,7 +688,9 @@ __global__ void __launch_bounds__(256) k_block_gemv(const C* __restrict__ inv, c
     const C* row = D + (long long)i * m;
     C a1 = czero<C>(), a2 = czero<C>();
     for (int j = lane; j < m; j += 32) {
-      const C d = row[j];
+      // streamed once per application: evict-first, so that the blocks do
+      // not push the Krylov basis out of L2
+      const C d = __ldcs(row + j);
       cfma(a1, d, r[j]);
       if (pair) cfma(a2, d, r[m + j]);
     }
@@ -1073,6 +1076,69 @@ vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool
   return VIE_OK;
 }
 
+// the kept-block product of a 1-level box with `split` CTAs per block (0: the
+// default rule, enough CTAs for about four per SM)
+template <class C>
+static vie_status launch_block_gemv(BoxPrec& B, const C* inv, const C* rh, C* zh, int split, cudaStream_t st) {
+  const int m = B.m;
+  const size_t smem = sizeof(C) * 2 * m;
+  if (split <= 0) split = std::max(1, std::min(8, (4 * 152 + B.nhalf - 1) / B.nhalf));
+  Prof pf_(sizeof(C) == 8 ? "block_gemv_c64" : "block_gemv_c128", st);
+  dim3 grid(B.nhalf, split);
+  k_block_gemv<C><<<grid, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, B.n, B.b.ny * B.b.nz);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+// autotuner: CTAs per block of the kept-block product (every split computes
+// each output row with one warp in the same order, so results do not depend
+// on the choice); timed on the box's own blocks, cached per shape
+template <class C>
+static vie_status tune_gemv(vie_plan_s* P, BoxPrec& B, int pi) {
+  if (B.nhalf <= 0 || !autotune_enabled()) return VIE_OK;
+  const TuneKey key{1, pi, B.m, B.nhalf, B.n};
+  int choice;
+  std::string rep;
+  if (!tune_cache_get(key, &choice, &rep)) {
+    C* inv = (C*)(pi == 0 ? B.inv64.p : B.inv128.p);
+    C* rh = (C*)(pi == 0 ? B.rhat64.p : B.rhat128.p);
+    C* zh = (C*)(pi == 0 ? B.zhat64.p : B.zhat128.p);
+    VIE_CUDA(cudaMemsetAsync(rh, 0, sizeof(C) * (size_t)B.n * B.m, P->st));
+    char buf[160];
+    snprintf(buf, sizeof(buf), "block_gemv_%s m=%d blocks=%d n=%d:", pi == 0 ? "c64" : "c128", B.m, B.nhalf, B.n);
+    rep = buf;
+    int best = 0;
+    float tbest = 0;
+    cudaEvent_t e0, e1;
+    VIE_CUDA(cudaEventCreate(&e0));
+    VIE_CUDA(cudaEventCreate(&e1));
+    for (int split : {1, 2, 4, 8}) {
+      if (split > 1 && B.m / split < 16) break;
+      VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, split, P->st));
+      cudaEventRecord(e0, P->st);
+      for (int r = 0; r < 3; ++r) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, split, P->st));
+      cudaEventRecord(e1, P->st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3;
+      snprintf(buf, sizeof(buf), " split %d %.4f ms;", split, ms);
+      rep += buf;
+      if (best == 0 || ms < tbest) { best = split; tbest = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    snprintf(buf, sizeof(buf), " chosen %d\n", best);
+    rep += buf;
+    choice = best;
+    tune_cache_put(key, choice, rep);
+  }
+  B.gemv_split = choice;
+  P->tuning += rep;
+  return VIE_OK;
+}
+
 static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128) {
   const BoxDims bd = dims_of(P, B.b);
   cudaStream_t st = P->st;
@@ -1163,11 +1229,14 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     const size_t ts = fft_scratch_elems<double2>(*B.fx, m);
     if (ts) VIE_TRY(B.tmp128.alloc(sizeof(double2) * ts));
   }
+  if (want64) VIE_TRY(tune_gemv<float2>(P, B, 0));
+  if (want128) VIE_TRY(tune_gemv<double2>(P, B, 1));
   return VIE_OK;
 }
 
 vie_status precond_build(vie_plan_s* P) {
   reset_graphs(P);   // captured Arnoldi steps point at the old blocks
+  P->tuning = P->tuning.substr(0, P->tuning_matvec);
   if (!P->side) {
     VIE_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
     VIE_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
@@ -1267,14 +1336,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
         VIE_CHECK_LAUNCH();
       }
     }
-    if (B.nhalf > 0) {
-      const size_t smem = sizeof(C) * 2 * m;
-      Prof pf_(sizeof(C) == 8 ? "block_gemv_c64" : "block_gemv_c128", st);
-      dim3 grid(B.nhalf, std::max(1, std::min(8, (4 * 152 + B.nhalf - 1) / B.nhalf)));
-      k_block_gemv<C><<<grid, 256, smem, st>>>(inv, B.blkf.as<int>(), rh, zh, m, n, nyb * nzb);
-      count_launch();
-      VIE_CHECK_LAUNCH();
-    }
+    if (B.nhalf > 0) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, B.gemv_split, st));
     if (tc) {
       VIE_CUDA(cudaEventRecord(P->ev_join, P->side));
       VIE_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));

@@ -84,6 +84,7 @@ _SIGS = {
     "vie_matvec_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "vie_plan_tuning": (ctypes.c_char_p, [ctypes.c_void_p]),
     "vie_last_error": (ctypes.c_char_p, []),
     "vie_kernel_launches": (ctypes.c_int64, []),
     "vie_profile_enable": (None, [ctypes.c_int]),
@@ -235,6 +236,11 @@ def vie_matvec_static(nx, ny, nz, h, k0, eps_bg, eps_ptr: int, x_ptr: int, y_ptr
     libvie); returns the status code unchanged."""
     return lib().vie_matvec_static(nx, ny, nz, h, k0, eps_bg, ctypes.c_void_p(eps_ptr), ctypes.c_void_p(x_ptr),
                                    ctypes.c_void_p(y_ptr), ctypes.c_void_p(stream))
+
+
+def vie_plan_tuning(plan) -> str:
+    """The autotuner's report for the plan (candidates, times, choices)."""
+    return (lib().vie_plan_tuning(plan) or b"").decode()
 
 
 def vie_kernel_launches() -> int:

@@ -6,7 +6,8 @@ discrete_form) that the GPU solves are compared with.
 * long_straight_1024x16x8: the oracle's right-preconditioned GMRES(50) on its
   FFT matvec to the relative residual 1e-12 (oracle.solve.iterative_solve);
   the solution does not depend on the preconditioner.  Stored whole.
-* larger workloads (4096x24x8 Bragg grating, 2048x48x8 coupler): the same
+* larger workloads (4096x24x8 Bragg grating, 2048x48x8 coupler at the first
+  wavelength of its batch, 1.50 um): the same
   iterative solve; stored as a seeded sample of 4096 entries plus the
   solution's 2-norm and max-abs, since the whole vector (38 MB) is too large
   to keep in the repository.
@@ -38,7 +39,7 @@ WORKLOADS = {
     "small_straight_64x8x4": inputs.workload_small_straight,
     "long_straight_1024x16x8": inputs.workload_long_straight,
     "bragg_4096x24x8_2boxes": inputs.workload_bragg,
-    "coupler_2048x48x8_2boxes": inputs.workload_coupler,
+    "coupler_2048x48x8_2boxes_lambda1.50": lambda: inputs.workload_coupler(wavelength=1.50),
 }
 FULL = {"small_straight_64x8x4", "long_straight_1024x16x8"}
 

@@ -1,0 +1,70 @@
+"""The autotuner (GPU): at plan creation it times the x-pass variants of the
+matvec -- the compile-time radix-16 kernel where one exists and the generic
+Stockham kernel with three radix orders -- and at preconditioner build the
+kept-block product's CTAs per block; it reports candidates, times and the
+choice, caches the choice per shape, and the tuned plan still matches the
+oracle."""
+import math
+import re
+
+import numpy as np
+import pytest
+
+from gpu_common import cuda_or_fail, maxerr, relerr
+from oracle import operator as op
+from paper_1903_07884_gb300 import inputs, vie
+from paper_1903_07884_gb300.solver import Plan, make_opts, to_device
+
+pytestmark = pytest.mark.gpu
+
+K0 = 2 * math.pi / 1.55
+
+
+def _xpass_lines(report, tag):
+    return [ln for ln in report.splitlines() if ln.startswith(tag)]
+
+
+@pytest.mark.parametrize("nx,ct", [(1024, True), (2031, True), (700, False)])
+def test_x_pass_candidates_timed_and_chosen(nx, ct):
+    cuda_or_fail()
+    ny, nz = 4, 2
+    eps = inputs.random_permittivity(nz, ny, nx, seed=nx)
+    x = inputs.random_field((3, nz, ny, nx), seed=nx + 1)
+    plan = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    rep = vie.vie_plan_tuning(plan.handle)
+    lines = _xpass_lines(rep, "x_pass_c64")
+    assert len(lines) == 1, rep
+    names = re.findall(r" (radix16x16x\d+|stockham\[[0-9.]+\]) ([0-9.]+) ms;", lines[0])
+    # distinct radix orders only (a palindromic order is timed once)
+    assert len(names) == len(set(n for n, _ in names)) and len(names) >= (3 if ct else 2), lines[0]
+    assert (names[0][0].startswith("radix16")) == ct
+    assert all(float(t) > 0 for _, t in names)
+    chosen = int(re.search(r"chosen (\d+)", lines[0]).group(1))
+    assert (0 if ct else 1) <= chosen <= 3
+    assert _xpass_lines(rep, "x_pass_c128"), rep
+    # the choice is cached per shape: a second plan reports the same
+    plan2 = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    assert _xpass_lines(vie.vie_plan_tuning(plan2.handle), "x_pass_c64") == lines
+    plan2.close()
+    # whatever variant was chosen, the matvec matches the oracle
+    plan.set_permittivity(eps)
+    y = plan.matvec(to_device(x), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    M = op.material(eps, 1.0)
+    ref = op.fft_matvec(x, M, op.generator_spectra(nx, ny, nz, 0.025, op.background_k(K0, 1.0)))
+    assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6
+
+
+def test_gemv_split_tuned_at_build():
+    cuda_or_fail()
+    p = inputs.straight_guide(320, 16, 8, 0.025, 1.55)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=1e-3)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    rep = vie.vie_plan_tuning(plan.handle)
+    lines = _xpass_lines(rep, "block_gemv_c64")
+    plan.close()
+    assert len(lines) == 1, rep
+    splits = re.findall(r"split (\d) ([0-9.]+) ms;", lines[0])
+    assert [int(s) for s, _ in splits] == [1, 2, 4, 8]
+    assert int(re.search(r"chosen (\d+)", lines[0]).group(1)) in (1, 2, 4, 8)

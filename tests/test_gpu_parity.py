@@ -59,12 +59,14 @@ def test_matvec_fp64_matches_oracle(shape, eps_bg):
         assert relerr(y, op.dense_matvec(A, x)) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4), (1013, 3, 2), (16, 100, 11), (1, 128, 33)])
+@pytest.mark.parametrize("shape", [(5, 3, 2), (64, 8, 4), (100, 12, 4), (1013, 3, 2), (2031, 3, 2), (2048, 4, 2),
+                                   (16, 100, 11), (1, 128, 33)])
 def test_matvec_mixed_matches_oracle(shape):
-    """(1013, 3, 2): a ragged nx whose embedding is L = 2048, the compile-time
-    radix-16 x pass (zero padding and crop at a non-aligned edge).  The last
-    two have Py Pz > 4096 (split y and z passes; with nx = 1 the y-lines of
-    Py = 256 are contiguous and take the warp-register FFT)."""
+    """(1013, 3, 2) and (2031, 3, 2): ragged nx whose embeddings are L = 2048
+    and 4096, the compile-time radix-16 x passes (zero padding and crop at a
+    non-aligned edge); (2048, 4, 2) the full 4096 line.  The last two have
+    Py Pz > 4096 (split y and z passes; with nx = 1 the y-lines of Py = 256
+    are contiguous and take the warp-register FFT)."""
     cuda_or_fail()
     nx, ny, nz = shape
     eps = inputs.random_permittivity(nz, ny, nx, seed=11)
