@@ -533,6 +533,14 @@ def run_gpu(args):
     if ref is not None:
         line["accuracy"] = {"vs_oracle_solution": "tests/golden (oracle GMRES to relres 1e-12)",
                             "mixed": solution_errors(w_mixed, ref), "fp64_gpu": solution_errors(w64, ref)}
+    else:
+        smp = oracle_solution_sample(wname)
+        if smp is not None:
+            idx, wref = smp
+            line["accuracy"] = {"vs_oracle_solution": f"tests/golden sample of {idx.size} entries (oracle GMRES "
+                                                      "to relres 1e-12)",
+                                "mixed": solution_errors(w_mixed.ravel()[idx], wref),
+                                "fp64_gpu": solution_errors(w64.ravel()[idx], wref)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S = OracleSample(p)
         restart = 50
@@ -607,7 +615,13 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
     span = max(t_done.values()) - min(t_arr.values())
     ok = sum(1 for s in status.values() if s in (vie.VIE_OK, vie.VIE_ENOCONV))
     converged = sum(1 for s in status.values() if s == vie.VIE_OK)
-    out = {"requests": len(reqs), "ok": ok, "converged": converged, "solves_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+    unconverged = [{"request": i, "kind": reqs[i].kind, "grid": [reqs[i].nx, reqs[i].ny, reqs[i].nz],
+                    "lambda_um": round(reqs[i].wavelength, 5), "relres": infos[i].relres,
+                    "iters": infos[i].iters_inner, "status": int(status[i])}
+                   for i in sorted(infos) if status.get(i) != vie.VIE_OK]
+    out = {"requests": len(reqs), "ok": ok, "converged": converged, "unconverged": unconverged,
+           "solves_per_s": len(reqs) / span, "converged_solves_per_s": converged / span,
+           "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "max_inflight": inflight, "budget_gb": budget_gb,
            "mean_iters": float(np.mean([infos[i].iters_inner for i in infos])) if infos else None,
            "max_relres": float(max(infos[i].relres for i in infos)) if infos else None}

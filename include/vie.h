@@ -252,12 +252,15 @@ vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double
                              const void* x_dev, void* y_dev, void* cuda_stream);
 
 /* The autotuner's report for the plan: per tuned kernel the shape, each
- * candidate launch variant with its measured device time (ms) and the index
- * chosen -- the matvec's x pass (compile-time radix-16 kernel or the generic
- * Stockham kernel with one of three radix orders, per precision), timed at
- * plan creation, and each box's kept-block product (1, 2, 4 or 8 CTAs per
+ * candidate launch variant with its measured device time (ms) and the
+ * choice -- the matvec's register yz passes (16, 8 or 4 x-columns per CTA)
+ * and its x pass (compile-time radix-16 kernel or the generic Stockham
+ * kernel with one of three radix orders, per precision), timed at plan
+ * creation, and each box's kept-block product (1, 2, 4 or 8 CTAs per
  * block), timed at preconditioner build.  Choices are cached per process and
- * shape; VIE_AUTOTUNE=0 in the environment keeps the default rules.  The
+ * shape; VIE_AUTOTUNE=0 in the environment keeps the default rules, and a
+ * file named by VIE_TUNE_FILE keeps the choices across processes (read at
+ * the first lookup, appended to by each new choice).  The
  * string belongs to the plan (valid until it is destroyed or rebuilt). */
 const char* vie_plan_tuning(vie_plan_t plan);
 

@@ -100,6 +100,7 @@ struct vie_plan_s {
   // generic Stockham kernel with radix order xord[.][k - 1])
   int xvar[2] = {-1, -1};
   vie::FftPlanDev xord[2][3]{};
+  int yzxg = 0;                        // x-columns per CTA of the register yz passes (0: 16)
   std::string tuning;                  // the autotuner's report (vie_plan_tuning)
   size_t tuning_matvec = 0;            // length of its matvec part (the rest belongs to the last build)
   vie::DevBuf spec128, spec64;         // [6][Pzh][Pyh][Lh] scaled generator spectra
@@ -140,6 +141,10 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
 vie_status matvec_alloc(vie_plan_s* P);
 template <class C>
 vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStream_t st);
+// both register yz passes (complex FP32) with xg x-columns per CTA on the
+// plan's staging buffers (autotuner timing); VIE_EINVAL if the cross-section
+// has no register variant
+vie_status yz_pair(vie_plan_s* P, int xg, cudaStream_t st);
 
 // tune.cu: per-shape choice among launch variants, by timing on the plan's
 // own buffers (cached per process and shape)
@@ -148,6 +153,31 @@ bool tune_cache_get(const TuneKey& k, int* choice, std::string* report);
 void tune_cache_put(const TuneKey& k, int choice, const std::string& report);
 vie_status tune_matvec(vie_plan_s* P);
 bool autotune_enabled();
+// device time of one call of f on stream st: after one warm-up call, the
+// least of three trials of reps back-to-back calls (a trial another stream's
+// work slowed down does not decide)
+template <class F>
+inline vie_status time_ms(cudaStream_t st, int reps, F f, float* ms) {
+  cudaEvent_t e0, e1;
+  VIE_CUDA(cudaEventCreate(&e0));
+  VIE_CUDA(cudaEventCreate(&e1));
+  vie_status s = f();
+  *ms = 0;
+  for (int trial = 0; trial < 3 && s >= 0; ++trial) {
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s >= 0; ++r) s = f();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    t /= (float)reps;
+    if (trial == 0 || t < *ms) *ms = t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
 
 // precond.cu
 vie_status precond_build(vie_plan_s* P);

@@ -325,20 +325,24 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2* __restrict__
 // partials and the plan's last CTA sums them (fixed order) into one vector
 // of dots; every CTA of the update pass derives the same coefficients from
 // it; one CTA per plan, on a second stream beside the update, keeps the
-// Hessenberg matrix and the Givens rotations; every CTA of the scale pass
-// sums the norm partials (fixed order) and its plan's last CTA to arrive
-// advances the step index.
+// Hessenberg matrix and the Givens rotations; one CTA per plan at the step end
+// sums the norm partials (fixed order) and advances the step index.  The
+// new direction w'' is left unnormalised in u
+// (the input of the next step's preconditioner); the step kernels scale u
+// and w = A P^-1 u by 1 / ||w''|| as they load them, so no pass rewrites the
+// vector after its norm is known.
 // ---------------------------------------------------------------------------
 constexpr int ARN_SUB = 16384;                  // bytes of one column per sub-chunk
 constexpr int ARN_THREADS = 512;                // streaming threads of the dot and update passes
-constexpr int SCALE_THREADS = 256;
+constexpr int STEP_END_THREADS = 128;
 
 // The vectors of one plan for the step kernels.
 template <class C>
 struct ArnPlan {
   C* V;            // basis: restart + 1 columns of stride ld
-  C* w;            // A P^-1 u_j on entry of the dot pass, w'' after the update pass
-  C* u;            // u_{j+1} = V_{j+1} after the scale pass (input of the next P^-1)
+  C* w;            // A P^-1 u_j, scaled by 1 / ||u_j|| (the GmresDev field inv_next)
+  C* u;            // u_j, unnormalised (w'' of step j - 1): input of P^-1; the update pass
+                   // writes w'' there
   GmresDev* s;     // GMRES state of the plan
   C* p1;           // [PST][NPART] dot partials (accumulator precision): row v, part b at v * NPART + b
   C* p2;           // [nparts] partials of ||w''||^2 (real part)
@@ -529,6 +533,11 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(const ArnPlan<C>* __res
   const int j = s->j;
   const C* __restrict__ V = dp->V;
   const C* __restrict__ w = dp->w;
+  const C* __restrict__ u = dp->u;
+  // u holds u_j unnormalised (w'' of the previous step) and w = A P^-1 of it:
+  // both are scaled by rho = 1 / ||w''|| as they are loaded
+  using R = typename real_of<C>::type;
+  const R rho = sizeof(R) == 4 ? (R)s->inv_next32 : (R)s->inv_next;
   const long long ld = dp->ld;
   const ArnRange g = arn_range<C>(dp->n3, dp->nparts, part);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -541,13 +550,13 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(const ArnPlan<C>* __res
     const long long start = g.c0 + (long long)sb * g.sc;
     const int cnt = min(g.sc, g.c1 - (int)start);
     const C* wv = w + start;
-    const C* uv = V + (long long)j * ld + start;
+    const C* uv = u + start;
     C xw[KPT], xu[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
       const int e = ct + q * ARN_THREADS;
-      xw[q] = e < cnt ? wv[e] : czero<C>();
-      xu[q] = e < cnt ? uv[e] : czero<C>();
+      xw[q] = e < cnt ? cscale(wv[e], rho) : czero<C>();
+      xu[q] = e < cnt ? cscale(uv[e], rho) : czero<C>();
     }
     C va[4][KPT], vb[4][KPT];
     if (j > 0) arn_load4<C, KPT>(va, V, ld, start, 0, min(4, j), ct, cnt);
@@ -758,10 +767,12 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
   {
     const ArnRange g = arn_range<C>(dp->n3, np, part);
     C* __restrict__ V = dp->V;
-    C* __restrict__ w = dp->w;
+    const C* __restrict__ w = dp->w;
+    C* __restrict__ u = dp->u;
     const long long ld = dp->ld;
     using R = typename real_of<C>::type;
     const R ibr = (R)ib;
+    const R rho = sizeof(R) == 4 ? (R)s->inv_next32 : (R)s->inv_next;   // scale of u and w (see the dot pass)
     const int ct = threadIdx.x;
     C* Vj = V + (long long)j * ld;
     // the sweep runs backwards (last sub-chunk, highest column first): the
@@ -791,8 +802,8 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
 #pragma unroll
       for (int q = 0; q < KPT; ++q) {
         const int e = ct + q * ARN_THREADS;
-        xw[q] = e < cnt ? w[start + e] : czero<C>();
-        xu[q] = e < cnt ? Vj[start + e] : czero<C>();
+        xw[q] = e < cnt ? cscale(w[start + e], rho) : czero<C>();
+        xu[q] = e < cnt ? cscale(u[start + e], rho) : czero<C>();
       }
 #pragma unroll
       for (int q = 0; q < KPT; ++q) {
@@ -805,7 +816,7 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
           x.x *= ibr;
           x.y *= ibr;
           Vj[start + e] = qj;
-          w[start + e] = x;
+          u[start + e] = x;   // u_{j+1} unnormalised: the next step scales it by 1 / ||w''||
           nrm += x.x * x.x + x.y * x.y;
         }
       }
@@ -821,23 +832,22 @@ __global__ void __maxnreg__(104) k_arn_update(const ArnPlan<C>* __restrict__ D, 
   }
 }
 
-// Scale pass: every CTA sums its plan's norm partials (same fixed order),
-// nu = ||w''||, and writes V_{j+1} = u = w'' / nu over its range.  The last
-// CTA of the plan to finish records nu as the tentative h_{j+1,j} and
-// advances j (no CTA of this launch reads j after it arrived).  nu = 0 is a
-// breakdown: the Krylov space is invariant, column j is final, and the cycle
-// ends.
+// Step end, one CTA per plan (after the update pass and the Hessenberg
+// bookkeeping): nu = ||w''|| from the norm partials (fixed order) becomes the
+// tentative h_{j+1,j} and 1 / nu the scale at which the next step reads
+// u_{j+1} = w'' (left unnormalised in u by the update pass) and w = A P^-1 of
+// it; j advances.  nu = 0 is a breakdown: the Krylov space is invariant,
+// column j is final, and the cycle ends.
 template <class C>
-__global__ void __launch_bounds__(SCALE_THREADS) k_arn_scale(const ArnPlan<C>* __restrict__ D, int nd) {
+__global__ void __launch_bounds__(STEP_END_THREADS) k_arn_step_end(const ArnPlan<C>* __restrict__ D) {
   using T = typename Acc<C>::T;
   constexpr int NPL = (NPART + 31) / 32;
-  __shared__ double nn_s;
-  int part;
-  const ArnPlan<C>* dp = arn_find(D, nd, part);
+  const ArnPlan<C>* dp = D + blockIdx.x;
   GmresDev* s = dp->s;
   if (s->done) return;
   const int j = s->j;
   const int lane = threadIdx.x & 31;
+  __shared__ double nn_s;
   if (threadIdx.x < 32) {
     const C* p2 = dp->p2;
     T v[NPL];
@@ -854,23 +864,7 @@ __global__ void __launch_bounds__(SCALE_THREADS) k_arn_scale(const ArnPlan<C>* _
   }
   __syncthreads();
   const double nu = sqrt(nn_s);
-  if (nu > 0.0) {
-    const ArnRange g = arn_range<C>(dp->n3, dp->nparts, part);
-    using R = typename real_of<C>::type;
-    const double invd = 1.0 / nu;
-    const R inv = (R)invd;   // reciprocal rounded to the vector precision
-    const C* __restrict__ w = dp->w;
-    C* __restrict__ Vn = dp->V + (long long)(j + 1) * dp->ld;
-    C* __restrict__ u = dp->u;
-    for (int e = g.c0 + threadIdx.x; e < g.c1; e += blockDim.x) {
-      const C x = cscale(w[e], inv);
-      Vn[e] = x;
-      u[e] = x;
-    }
-  }
-  if (!last_block_of(&s->arrive_upd, dp->nparts)) return;
   if (nu == 0.0) {
-    // breakdown: the Krylov space is invariant and column j is already final
     if (threadIdx.x == 0) {
       s->nu = 0.0;
       s->Hr[(long long)j * (RMAX + 1) + j + 1] = make_double2(0.0, 0.0);
@@ -917,6 +911,8 @@ __global__ void k_cycle_init(GmresDev* __restrict__ s, const double2* __restrict
   s->resest = beta;
   s->reorth = 0;
   s->nu = 0;
+  s->inv_next = 1.0;      // V_0 = u = r / beta is stored normalised
+  s->inv_next32 = 1.0f;
   s->arrive_dot = 0;
   s->arrive_upd = 0;
   for (int i = 0; i <= restart; ++i) s->g[i] = make_double2(0, 0);
@@ -1220,7 +1216,7 @@ static vie_status arn_launch(const ArnPlan<C>* D, int nd, int ncta, cudaStream_t
     k_arn_update<C><<<ncta, ARN_THREADS, 0, st>>>(D, nd);
   }
   VIE_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
-  { Prof pf_("arnoldi_scale", st); k_arn_scale<C><<<ncta, SCALE_THREADS, 0, st>>>(D, nd); }
+  { Prof pf_("arnoldi_step_end", st); k_arn_step_end<C><<<nd, STEP_END_THREADS, 0, st>>>(D); }
   count_launch(4);
   VIE_CHECK_LAUNCH();
   return VIE_OK;
@@ -1356,10 +1352,12 @@ vie_status gmres_done<float2>(Run& R) {
     return VIE_ECUDA;
   }
   if (it == 0) return run_finish(R);
-  // a step that does not reduce the FP64 residual by 10% (twice in a row)
-  // means the inner solve has nothing left to give
-  if (R.rn > 0.9 * R.rn_prev) {
-    if (++R.ir_stalls >= 2) return run_finish(R);
+  // three refinement steps in a row that do not reduce the FP64 residual by
+  // 1% mean the inner solve has nothing left to give (the rule of the FP64
+  // GMRES restarts; a hard operator may gain only a few percent per cycle
+  // and still converge)
+  if (R.rn > 0.99 * R.rn_prev) {
+    if (++R.ir_stalls >= 3) return run_finish(R);
   } else {
     R.ir_stalls = 0;
   }

@@ -5,4 +5,15 @@ namespace vie {
 template vie_status matvec<float2>(vie_plan_s*, const float2*, float2*, const float2*, const float2*, float2*,
                                    float2*, cudaStream_t);
 template vie_status xpass<float2>(vie_plan_s*, const float2*, float2*, float2*, int, cudaStream_t);
+
+vie_status yz_pair(vie_plan_s* P, int xg, cudaStream_t st) {
+  const int yzr = yz_variant(P->d);
+  if (!yzr || P->yz_split) return VIE_EINVAL;
+  float2* x = P->xin64.as<float2>();
+  float2* y = P->xout64.as<float2>();
+  float2* T = P->T64.as<float2>();
+  VIE_TRY(yz_r_launch(P->d, yzr, xg, true, x, T, nullptr, nullptr, nullptr, st));
+  // (the staging vector stands in for M: only the timing matters here)
+  return yz_r_launch(P->d, yzr, xg, false, nullptr, nullptr, T, x, y, st, x);
+}
 }  // namespace vie

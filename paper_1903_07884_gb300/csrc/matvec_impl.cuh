@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(R2 * R3, 512 / (R2 * R3)) k_mv_x16(float2* __r
 
 // ---------------------------------------------------------------------------
 // yz passes for power-of-two Py, Pz (<= 32) in complex FP32: one transform per
-// thread in registers (radix-2 decimation in time), XG = 16 x-columns per CTA,
+// thread in registers (radix-2 decimation in time), YZ_XG x-columns per CTA,
 // one shared-memory exchange between the y and the z transforms.  Shared
 // memory holds the y spectra of the nz non-zero z rows as [z][xl][ky] with a
 // pitch of Py + 1, so both the row writes and the column reads are
@@ -419,9 +419,11 @@ __device__ __forceinline__ void dft_p2(float2 (&v)[N]) {
   for (int i = 0; i < N; ++i) v[i] = a[i];
 }
 
-constexpr int YZ_XG = 16;
+// x-columns per CTA of the register yz passes: a template parameter, chosen
+// per shape by the autotuner among 16, 8 and 4 (every choice transforms the
+// same columns the same way)
 
-template <int PY, int PZ>
+template <int PY, int PZ, int YZ_XG>
 __global__ void __launch_bounds__(128) k_mv_yz_fwd_r(const float2* __restrict__ x, float2* __restrict__ T, MvDims d) {
   constexpr int PITCH = PY + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(128) k_mv_yz_fwd_r(const float2* __restrict__ 
   }
 }
 
-template <int PY, int PZ>
+template <int PY, int PZ, int YZ_XG>
 __global__ void __launch_bounds__(128) k_mv_yz_inv_r(const float2* __restrict__ T, const float2* __restrict__ x,
                                                      const float2* __restrict__ Mv, float2* __restrict__ y, MvDims d) {
   constexpr int PITCH = PY + 1;
@@ -615,6 +617,36 @@ static vie_status set_smem(K kern, size_t smem) {
     default: set_error("matvec: tile too large for one block"); return VIE_EINVAL; \
   }
 
+// Register yz pass (forward: x -> T; inverse: T -> y with the epilogue) for
+// cross-section variant yzr (1: Py 32 x Pz 16, 2: 16 x 8) and xg x-columns per
+// CTA (16, 8 or 4).
+static inline vie_status yz_r_launch(const MvDims& d, int yzr, int xg, bool fwd, const float2* x, float2* T,
+                                     const float2* Ti, const float2* Mv, float2* y, cudaStream_t st,
+                                     const float2* xi = nullptr) {
+  const int py = yzr == 1 ? 32 : 16;
+  const size_t smem = (size_t)d.nz * xg * (py + 1) * sizeof(float2);
+  const dim3 g(ceil_div(d.nx, xg), 3);
+#define VIE_YZ(PY, PZ, XG)                                                                          \
+  if (fwd) k_mv_yz_fwd_r<PY, PZ, XG><<<g, 128, smem, st>>>(x, T, d);                                \
+  else k_mv_yz_inv_r<PY, PZ, XG><<<g, 128, smem, st>>>(Ti, xi, Mv, y, d);
+  {
+    Prof pf_(fwd ? "mv_yz_fwd_c64" : "mv_yz_inv_c64", st);
+    if (yzr == 1) {
+      if (xg == 16) { VIE_YZ(32, 16, 16) } else if (xg == 8) { VIE_YZ(32, 16, 8) } else { VIE_YZ(32, 16, 4) }
+    } else {
+      if (xg == 16) { VIE_YZ(16, 8, 16) } else if (xg == 8) { VIE_YZ(16, 8, 8) } else { VIE_YZ(16, 8, 4) }
+    }
+  }
+#undef VIE_YZ
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+// register yz variant of a cross-section (0: none)
+static inline int yz_variant(const MvDims& d) {
+  return (d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0;
+}
+
 // The x pass alone (pass B of the matvec) in one of its variants: T holds
 // the yz-transformed field on entry and the inverse x-transformed product on
 // exit.  The autotuner times the variants with this entry.
@@ -696,9 +728,8 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   dim3 gA(ceil_div(d.nx, XG), 3);
   const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);
   // register transforms for the power-of-two cross-sections that have an instantiation
-  const int yzr = sizeof(C) == 8 ? ((d.Py == 32 && d.Pz == 16) ? 1 : (d.Py == 16 && d.Pz == 8) ? 2 : 0) : 0;
-  const size_t smemR = (size_t)d.nz * YZ_XG * (d.Py + 1) * sizeof(float2);
-  const dim3 gR(ceil_div(d.nx, YZ_XG), 3);
+  const int yzr = sizeof(C) == 8 ? yz_variant(d) : 0;
+  const int yzxg = P->yzxg > 0 ? P->yzxg : 16;
   C* U = (C*)(sizeof(C) == 16 ? P->U128.p : P->U64.p);
   const long long pyx = (long long)d.Py * d.nx;
   if (P->yz_split) {
@@ -710,9 +741,7 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     LineDesc dz{d.nz, d.Pz, (int)(3 * pyx), (int)pyx, 3, 1, d.nz * pyx, 0, pyx, 1, d.Pz * pyx, 0, pyx};
     VIE_TRY(fft_lines<C>(U, T, dz, *P->fPz, -1, 1.0, nullptr, st));
   } else if (yzr) {
-    Prof pf_("mv_yz_fwd_c64", st);
-    if (yzr == 1) k_mv_yz_fwd_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
-    else k_mv_yz_fwd_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)x, (float2*)T, d);
+    VIE_TRY(yz_r_launch(d, yzr, yzxg, true, (const float2*)x, (float2*)T, nullptr, nullptr, nullptr, st));
   } else {
     auto k = k_mv_yz_fwd<C>;
     VIE_TRY(set_smem(k, smemA));
@@ -739,11 +768,8 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
     return VIE_OK;
   }
   if (yzr) {
-    Prof pf_("mv_yz_inv_c64", st);
-    if (yzr == 1)
-      k_mv_yz_inv_r<32, 16><<<gR, 128, smemR, st>>>((const float2*)T, (const float2*)x, (const float2*)Mv, (float2*)y, d);
-    else
-      k_mv_yz_inv_r<16, 8><<<gR, 128, smemR, st>>>((const float2*)T, (const float2*)x, (const float2*)Mv, (float2*)y, d);
+    VIE_TRY(yz_r_launch(d, yzr, yzxg, false, nullptr, nullptr, (const float2*)T, (const float2*)Mv, (float2*)y, st,
+                        (const float2*)x));
   } else {
     auto k = k_mv_yz_inv<C>;
     VIE_TRY(set_smem(k, smemA));

@@ -1110,25 +1110,14 @@ static vie_status tune_gemv(vie_plan_s* P, BoxPrec& B, int pi) {
     rep = buf;
     int best = 0;
     float tbest = 0;
-    cudaEvent_t e0, e1;
-    VIE_CUDA(cudaEventCreate(&e0));
-    VIE_CUDA(cudaEventCreate(&e1));
     for (int split : {1, 2, 4, 8}) {
       if (split > 1 && B.m / split < 16) break;
-      VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, split, P->st));
-      cudaEventRecord(e0, P->st);
-      for (int r = 0; r < 3; ++r) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, split, P->st));
-      cudaEventRecord(e1, P->st);
-      cudaEventSynchronize(e1);
       float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= 3;
+      VIE_TRY(time_ms(P->st, 3, [&] { return launch_block_gemv<C>(B, inv, rh, zh, split, P->st); }, &ms));
       snprintf(buf, sizeof(buf), " split %d %.4f ms;", split, ms);
       rep += buf;
       if (best == 0 || ms < tbest) { best = split; tbest = ms; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     snprintf(buf, sizeof(buf), " chosen %d\n", best);
     rep += buf;
     choice = best;

@@ -1,5 +1,8 @@
 // Autotuner.  For the shapes of a plan it times the candidate launch variants
-// of two kernels on the plan's own buffers and keeps the fastest:
+// of three kernels on the plan's own buffers and keeps the fastest:
+//   * the matvec's register yz passes (complex FP32, power-of-two
+//     cross-sections): 16, 8 or 4 x-columns per CTA (every choice transforms
+//     the same columns the same way, so results do not depend on it);
 //   * the matvec's x pass (per precision): the compile-time radix-16 kernel
 //     where one exists (complex FP32, L = 2048 or 4096) and the generic
 //     shared-memory Stockham kernel with three radix orders of L (8s first;
@@ -9,8 +12,9 @@
 //     so the results do not depend on the choice).
 // Choices are cached per process and shape, so all plans of a shape run the
 // same kernels (a plan solved alone and in a batch stays bitwise the same).
-// VIE_AUTOTUNE=0 in the environment keeps the default rules.  The report of
-// a plan's choices and timings is returned by vie_plan_tuning.
+// VIE_AUTOTUNE=0 in the environment keeps the default rules; VIE_TUNE_FILE
+// keeps the choices across processes.  The report of a plan's choices and
+// timings is returned by vie_plan_tuning.
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -33,9 +37,33 @@ bool autotune_enabled() {
 
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<int, std::string>> g_tune;
+static bool g_tune_loaded = false;
+
+// VIE_TUNE_FILE names a file of earlier choices ("kernel precision a b c
+// choice" per line) read at the first lookup; new choices are appended to it,
+// so that another process (a profiler run, say) reuses them.
+static const char* tune_file() {
+  const char* f = getenv("VIE_TUNE_FILE");
+  return (f && f[0]) ? f : nullptr;
+}
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* fn = tune_file();
+  if (!fn) return;
+  FILE* f = fopen(fn, "r");
+  if (!f) return;
+  int k, p, a, b, c, ch;
+  while (fscanf(f, "%d %d %d %d %d %d", &k, &p, &a, &b, &c, &ch) == 6)
+    g_tune.emplace(TuneKey{k, p, a, b, c}, std::make_pair(ch, std::string("(from VIE_TUNE_FILE) chosen ") +
+                                                                  std::to_string(ch) + "\n"));
+  fclose(f);
+}
 
 bool tune_cache_get(const TuneKey& k, int* choice, std::string* report) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
   auto it = g_tune.find(k);
   if (it == g_tune.end()) return false;
   *choice = it->second.first;
@@ -45,27 +73,15 @@ bool tune_cache_get(const TuneKey& k, int* choice, std::string* report) {
 
 void tune_cache_put(const TuneKey& k, int choice, const std::string& report) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune.emplace(k, std::make_pair(choice, report));
-}
-
-// mean device time of reps calls of f after one warm-up call, on stream st
-template <class F>
-static vie_status time_ms(cudaStream_t st, int reps, F f, float* ms) {
-  cudaEvent_t e0, e1;
-  VIE_CUDA(cudaEventCreate(&e0));
-  VIE_CUDA(cudaEventCreate(&e1));
-  vie_status s = f();
-  if (s >= 0) {
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < reps && s >= 0; ++r) s = f();
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(ms, e0, e1);
-    *ms /= (float)reps;
+  tune_load_locked();
+  if (!g_tune.emplace(k, std::make_pair(choice, report)).second) return;
+  if (const char* fn = tune_file()) {
+    if (FILE* f = fopen(fn, "a")) {
+      fprintf(f, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+              std::get<4>(k), choice);
+      fclose(f);
+    }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return s;
 }
 
 // alternative radix orders of L (the twiddle table of the base plan serves all)
@@ -154,6 +170,42 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   return VIE_OK;
 }
 
+// x-columns per CTA of the register yz passes (forward and inverse timed
+// together; every choice transforms the same columns the same way)
+static vie_status tune_yz(vie_plan_s* P) {
+  const MvDims& d = P->d;
+  if (yz_pair(P, 16, P->st) == VIE_EINVAL) {
+    cudaGetLastError();
+    return VIE_OK;
+  }
+  const TuneKey key{2, 0, d.Py, d.Pz, d.nx * 64 + d.nz};
+  int choice;
+  std::string rep;
+  if (!tune_cache_get(key, &choice, &rep)) {
+    const long long n3 = 3LL * d.nx * d.ny * d.nz;
+    VIE_CUDA(cudaMemsetAsync(P->xin64.p, 0, sizeof(float2) * n3, P->st));
+    char buf[160];
+    snprintf(buf, sizeof(buf), "yz_passes_c64 nx=%d Py=%d Pz=%d nz=%d:", d.nx, d.Py, d.Pz, d.nz);
+    rep = buf;
+    int best = 0;
+    float tbest = 0;
+    for (int xg : {16, 8, 4}) {
+      float ms = 0;
+      VIE_TRY(time_ms(P->st, 3, [&] { return yz_pair(P, xg, P->st); }, &ms));
+      snprintf(buf, sizeof(buf), " %d columns/CTA %.4f ms;", xg, ms);
+      rep += buf;
+      if (best == 0 || ms < tbest) { best = xg; tbest = ms; }
+    }
+    snprintf(buf, sizeof(buf), " chosen %d\n", best);
+    rep += buf;
+    choice = best;
+    tune_cache_put(key, choice, rep);
+  }
+  P->yzxg = choice;
+  P->tuning += rep;
+  return VIE_OK;
+}
+
 vie_status tune_matvec(vie_plan_s* P) {
   if (!autotune_enabled()) {
     // default rule, with the radix orders filled in
@@ -163,6 +215,7 @@ vie_status tune_matvec(vie_plan_s* P) {
     P->tuning_matvec = P->tuning.size();
     return VIE_OK;
   }
+  VIE_TRY(tune_yz(P));
   VIE_TRY(tune_x<float2>(P, 0));
   VIE_TRY(tune_x<double2>(P, 1));
   VIE_CUDA(cudaStreamSynchronize(P->st));

@@ -68,3 +68,26 @@ def test_gemv_split_tuned_at_build():
     splits = re.findall(r"split (\d) ([0-9.]+) ms;", lines[0])
     assert [int(s) for s, _ in splits] == [1, 2, 4, 8]
     assert int(re.search(r"chosen (\d+)", lines[0]).group(1)) in (1, 2, 4, 8)
+
+
+def test_yz_columns_per_cta_tuned_for_register_cross_sections():
+    """16x8-voxel cross-sections (Py = 32, Pz = 16) take the register yz
+    passes; the tuner times 16, 8 and 4 x-columns per CTA and the matvec
+    stays within the complex-FP32 bound of the oracle for the choice made."""
+    cuda_or_fail()
+    nx, ny, nz = 300, 16, 8
+    plan = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    rep = vie.vie_plan_tuning(plan.handle)
+    lines = _xpass_lines(rep, "yz_passes_c64")
+    assert len(lines) == 1, rep
+    cols = re.findall(r" (\d+) columns/CTA ([0-9.]+) ms;", lines[0])
+    assert [int(c) for c, _ in cols] == [16, 8, 4]
+    assert int(re.search(r"chosen (\d+)", lines[0]).group(1)) in (16, 8, 4)
+    eps = inputs.random_permittivity(nz, ny, nx, seed=17)
+    x = inputs.random_field((3, nz, ny, nx), seed=18)
+    plan.set_permittivity(eps)
+    y = plan.matvec(to_device(x), vie.VIE_MIXED).cpu().numpy()
+    plan.close()
+    ref = op.fft_matvec(x, op.material(eps, 1.0),
+                        op.generator_spectra(nx, ny, nz, 0.025, op.background_k(K0, 1.0)))
+    assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6
