@@ -264,6 +264,16 @@ vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double
  * string belongs to the plan (valid until it is destroyed or rebuilt). */
 const char* vie_plan_tuning(vie_plan_t plan);
 
+/* Test hook: override one of the autotuner's choices for this plan.  kernel
+ * "x_pass_c64" / "x_pass_c128" with choice -1 (default rule), 0 (three-pass
+ * compile-time kernel, complex FP32, L = 2048 or 4096), 1..3 (generic
+ * Stockham kernel with radix order 1..3) or 4 (four-pass compile-time kernel,
+ * complex FP32, L = 4096 or 8192); "yz_passes_c64" with 16, 8 or 4 x-columns
+ * per CTA; "block_gemv" with 1, 2, 4 or 8 CTAs per kept block (set on the
+ * built preconditioner; a rebuild tunes again).  VIE_EINVAL for a variant that
+ * does not exist for the plan's shape. */
+vie_status vie_plan_set_tuning(vie_plan_t plan, const char* kernel, int choice);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* vie_last_error(void);
 

@@ -370,6 +370,210 @@ __global__ void __launch_bounds__(R2 * R3, 512 / (R2 * R3)) k_mv_x16(float2* __r
 }
 
 // ---------------------------------------------------------------------------
+// The same scheme with four passes, L = R1 R2 R3 R4 (R1 = R2, R3 and R4
+// dividing R1), for the longer power-of-two embeddings: pass 1 radix R1 at
+// stride L/R1 (twiddles W_L^{b q}), pass 2 radix R2 inside each block of L/R1
+// (W_{L/R1}^{b q}), pass 3 radix R3 inside each block of L/(R1 R2)
+// (W_{L/(R1 R2)}^{b q}), pass 4 on R4 contiguous points, which leaves
+// X[q1 + R1 q2 + R1 R2 q3 + R1 R2 R3 q4] at position q1 L/R1 + q2 L/(R1 R2) +
+// q3 R4 + q4; the tensor product works on that order and the inverse mirrors
+// the forward passes.  A thread takes one pass-1 and one pass-2 butterfly,
+// R1/R3 pass-3 butterflies and R1/R4 pass-4 groups, one component at a time
+// except in the product, so its registers stay few with L/R1 threads.
+// ---------------------------------------------------------------------------
+template <int R1, int R2, int R3, int R4>
+__global__ void __launch_bounds__(R1 * R2 * R3 * R4 / R1) k_mv_x4p(float2* __restrict__ T,
+                                                                 const float2* __restrict__ spec, MvDims d,
+                                                                 const float2* __restrict__ twL) {
+  constexpr int L = R1 * R2 * R3 * R4, NT = L / R1;
+  constexpr int S1 = L / R1, S2 = S1 / R2, S3 = S2 / R3;
+  constexpr int G3 = R1 / R3, G4 = R1 / R4;
+  constexpr int LP = L + L / 16;
+  static_assert(R1 == R2 && R1 % R3 == 0 && R1 % R4 == 0 && S3 == R4, "pass structure");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);   // [3][LP]
+  const int t = threadIdx.x;
+  const int kyz = blockIdx.x;
+  const int ky = kyz % d.Py, kz = kyz / d.Py;
+  const long long lstride = (long long)d.Pz * d.Py * d.nx;
+  const long long loff = ((long long)kz * d.Py + ky) * d.nx;
+  float2 v[R1];
+  // forward pass 1 from global memory (zero beyond nx); twiddles are read
+  // again where a pass repeats, so that none stay live across the product
+  {
+  float2 w[R1];
+#pragma unroll
+  for (int q = 1; q < R1; ++q) w[q] = twL[t * q];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = t + S1 * r;
+      v[r] = i < d.nx ? T[a * lstride + loff + i] : make_float2(0.f, 0.f);
+    }
+    dft_pow2<R1, -1>(v);
+#pragma unroll
+    for (int q = 1; q < R1; ++q) v[q] = cmul(v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < R1; ++q) sm[a * LP + xpad(t + S1 * q)] = v[q];
+  }
+  }
+  __syncthreads();
+  // forward pass 2: block q1 = t / S2, offset b2
+  const int b2 = t % S2, base2 = (t / S2) * S1;
+  {
+  float2 w2[R2];
+#pragma unroll
+  for (int q = 1; q < R2; ++q) w2[q] = twL[b2 * q * R1];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int r = 0; r < R2; ++r) v[r] = sm[a * LP + xpad(base2 + b2 + S2 * r)];
+    dft_pow2<R2, -1>(v);
+#pragma unroll
+    for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], w2[q]);
+#pragma unroll
+    for (int q = 0; q < R2; ++q) sm[a * LP + xpad(base2 + b2 + S2 * q)] = v[q];
+  }
+  }
+  __syncthreads();
+  // forward pass 3: G3 butterflies per thread, block of S2 points, offset b3
+#pragma unroll 1
+  for (int g = 0; g < G3; ++g) {
+    const int u3 = g * NT + t;                 // butterfly index < L / R3
+    const int b3 = u3 % S3, base3 = (u3 / S3) * S2;
+    float2 w3[R3];
+#pragma unroll
+    for (int q = 1; q < R3; ++q) w3[q] = twL[b3 * q * R1 * R2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 x3[R3];
+#pragma unroll
+      for (int r = 0; r < R3; ++r) x3[r] = sm[a * LP + xpad(base3 + b3 + S3 * r)];
+      dft_pow2<R3, -1>(x3);
+#pragma unroll
+      for (int q = 1; q < R3; ++q) x3[q] = cmul(x3[q], w3[q]);
+#pragma unroll
+      for (int q = 0; q < R3; ++q) sm[a * LP + xpad(base3 + b3 + S3 * q)] = x3[q];
+    }
+  }
+  __syncthreads();
+  // pass 4, the tensor product and the inverse pass 4 on G4 groups of R4 contiguous points
+  const bool fy = ky > d.Py / 2, fz = kz > d.Pz / 2;
+  const int kyo = fy ? d.Py - ky : ky;
+  const int kzo = fz ? d.Pz - kz : kz;
+  const long long Q = (long long)d.Lh * d.Pyh * d.Pzh;
+  float syz[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float sg = 1.f;
+    if (fy) sg *= pair_parity(c, 1);
+    if (fz) sg *= pair_parity(c, 2);
+    syz[c] = sg;
+  }
+#pragma unroll 1
+  for (int g = 0; g < G4; ++g) {
+    const int sb = g * NT + t;                 // group index < L / R4
+    const int base4 = sb * R4;
+    float2 u[3][R4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < R4; ++r) u[a][r] = sm[a * LP + xpad(base4 + r)];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dft_pow2<R4, -1>(u[a]);
+    // position base4 + q4 = q1 S1 + q2 S2 + q3 R4 + q4
+    const int q1 = base4 / S1, q2 = (base4 % S1) / S2, q3 = (base4 % S2) / R4;
+#pragma unroll
+    for (int q4 = 0; q4 < R4; ++q4) {
+      const int kx = q1 + R1 * q2 + R1 * R2 * q3 + R1 * R2 * R3 * q4;
+      const float2 X0 = u[0][q4], X1 = u[1][q4], X2 = u[2][q4];
+      const float2 gxx = spec_at(spec, 0, kx, kyo, kzo, syz[0], d, Q);
+      const float2 gxy = spec_at(spec, 1, kx, kyo, kzo, syz[1], d, Q);
+      const float2 gxz = spec_at(spec, 2, kx, kyo, kzo, syz[2], d, Q);
+      const float2 gyy = spec_at(spec, 3, kx, kyo, kzo, syz[3], d, Q);
+      const float2 gyz = spec_at(spec, 4, kx, kyo, kzo, syz[4], d, Q);
+      const float2 gzz = spec_at(spec, 5, kx, kyo, kzo, syz[5], d, Q);
+      float2 y0 = cmul(gxx, X0), y1 = cmul(gxy, X0), y2 = cmul(gxz, X0);
+      cfma(y0, gxy, X1); cfma(y1, gyy, X1); cfma(y2, gyz, X1);
+      cfma(y0, gxz, X2); cfma(y1, gyz, X2); cfma(y2, gzz, X2);
+      u[0][q4] = y0; u[1][q4] = y1; u[2][q4] = y2;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dft_pow2<R4, +1>(u[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < R4; ++r) sm[a * LP + xpad(base4 + r)] = u[a][r];
+  }
+  __syncthreads();
+  // inverse pass 3: conjugate twiddles, then conjugate butterflies
+#pragma unroll 1
+  for (int g = 0; g < G3; ++g) {
+    const int u3 = g * NT + t;
+    const int b3 = u3 % S3, base3 = (u3 / S3) * S2;
+    float2 w3[R3];
+#pragma unroll
+    for (int q = 1; q < R3; ++q) {
+      w3[q] = twL[b3 * q * R1 * R2];
+      w3[q].y = -w3[q].y;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 x3[R3];
+#pragma unroll
+      for (int q = 0; q < R3; ++q) x3[q] = sm[a * LP + xpad(base3 + b3 + S3 * q)];
+#pragma unroll
+      for (int q = 1; q < R3; ++q) x3[q] = cmul(x3[q], w3[q]);
+      dft_pow2<R3, +1>(x3);
+#pragma unroll
+      for (int r = 0; r < R3; ++r) sm[a * LP + xpad(base3 + b3 + S3 * r)] = x3[r];
+    }
+  }
+  __syncthreads();
+  // inverse pass 2
+  {
+  float2 w2[R2];
+#pragma unroll
+  for (int q = 1; q < R2; ++q) {
+    w2[q] = twL[b2 * q * R1];
+    w2[q].y = -w2[q].y;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int q = 0; q < R2; ++q) v[q] = sm[a * LP + xpad(base2 + b2 + S2 * q)];
+#pragma unroll
+    for (int q = 1; q < R2; ++q) v[q] = cmul(v[q], w2[q]);
+    dft_pow2<R2, +1>(v);
+#pragma unroll
+    for (int r = 0; r < R2; ++r) sm[a * LP + xpad(base2 + b2 + S2 * r)] = v[r];
+  }
+  }
+  __syncthreads();
+  // inverse pass 1, straight to global memory (the nx points kept)
+  float2 w[R1];
+#pragma unroll
+  for (int q = 1; q < R1; ++q) {
+    w[q] = twL[t * q];
+    w[q].y = -w[q].y;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int q = 0; q < R1; ++q) v[q] = sm[a * LP + xpad(t + S1 * q)];
+#pragma unroll
+    for (int q = 1; q < R1; ++q) v[q] = cmul(v[q], w[q]);
+    dft_pow2<R1, +1>(v);
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = t + S1 * r;
+      if (i < d.nx) T[a * lstride + loff + i] = v[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // yz passes for power-of-two Py, Pz (<= 32) in complex FP32: one transform per
 // thread in registers (radix-2 decimation in time), YZ_XG x-columns per CTA,
 // one shared-memory exchange between the y and the z transforms.  Shared
@@ -660,9 +864,26 @@ vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStre
     const size_t tile = (size_t)3 * d.L * sizeof(C);
     // variant 0 (or -1, untuned): the compile-time radix-16 kernel where one
     // exists; k >= 1: the generic Stockham kernel with radix order k - 1
+    // variant 4: the four-pass compile-time kernel (L = 4096 or 8192), also the
+    // default for L = 8192, which has no three-pass kernel
+    const bool fp = sizeof(C) == 8 && ((d.L == 4096 && variant == 4) || (d.L == 8192 && (variant == 4 || variant < 0)));
     const bool ct = sizeof(C) == 8 && (d.L == 2048 || d.L == 4096) && variant <= 0;
-    const FftPlanDev pl = variant >= 1 ? P->xord[sizeof(C) == 8 ? 0 : 1][variant - 1] : plan_of;
-    if (ct && d.L == 2048) {
+    const FftPlanDev pl = (variant >= 1 && variant <= 3) ? P->xord[sizeof(C) == 8 ? 0 : 1][variant - 1] : plan_of;
+    if (fp && d.L == 4096) {
+      constexpr int L = 4096;
+      const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);
+      Prof pf_("mv_x_c64", st);
+      VIE_TRY(set_smem(k_mv_x4p<16, 16, 4, 4>, smem));
+      k_mv_x4p<16, 16, 4, 4><<<d.Py * d.Pz, L / 16, smem, st>>>((float2*)T, (const float2*)spec, d,
+                                                                (const float2*)pl.tw);
+    } else if (fp && d.L == 8192) {
+      constexpr int L = 8192;
+      const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);
+      Prof pf_("mv_x_c64", st);
+      VIE_TRY(set_smem(k_mv_x4p<16, 16, 8, 4>, smem));
+      k_mv_x4p<16, 16, 8, 4><<<d.Py * d.Pz, L / 16, smem, st>>>((float2*)T, (const float2*)spec, d,
+                                                                (const float2*)pl.tw);
+    } else if (ct && d.L == 2048) {
       // compile-time radix structure 16 x 16 x 8 (complex FP32)
       constexpr int L = 2048;
       const size_t smem = 3 * (size_t)(L + L / 16) * sizeof(float2);

@@ -3,10 +3,11 @@
 //   * the matvec's register yz passes (complex FP32, power-of-two
 //     cross-sections): 16, 8 or 4 x-columns per CTA (every choice transforms
 //     the same columns the same way, so results do not depend on it);
-//   * the matvec's x pass (per precision): the compile-time radix-16 kernel
-//     where one exists (complex FP32, L = 2048 or 4096) and the generic
-//     shared-memory Stockham kernel with three radix orders of L (8s first;
-//     reversed; powers of two as 4s);
+//   * the matvec's x pass (per precision): the compile-time kernels where
+//     they exist (complex FP32: three passes 16x16x8 for L = 2048, 16x16x16
+//     for 4096; four passes 16x16x4x4 for 4096, 16x16x8x4 for 8192) and the
+//     generic shared-memory Stockham kernel with three radix orders of L (8s
+//     first; reversed; powers of two as 4s);
 //   * the kept-block product of each 1-level box: rows of a block split over
 //     1, 2, 4 or 8 CTAs (every split computes each output in the same order,
 //     so the results do not depend on the choice).
@@ -139,16 +140,18 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   const C* spec = (const C*)(pi == 0 ? P->spec64.p : P->spec128.p);
   const long long nT = 3LL * d.Pz * d.Py * d.nx;
   VIE_CUDA(cudaMemsetAsync(T, 0, sizeof(C) * nT, P->st));
-  const bool ct = pi == 0 && (d.L == 2048 || d.L == 4096);
+  const bool ct = pi == 0 && (d.L == 2048 || d.L == 4096);   // three-pass compile-time kernel (variant 0)
+  const bool fp = pi == 0 && (d.L == 4096 || d.L == 8192);   // four-pass compile-time kernel (variant 4)
   char buf[160];
   snprintf(buf, sizeof(buf), "%s L=%d Py=%d Pz=%d:", tag, d.L, d.Py, d.Pz);
   rep = buf;
   int best = -1;
   float tbest = 0;
-  for (int v = ct ? 0 : 1; v <= nord; ++v) {
+  for (int v = ct ? 0 : 1; v <= (fp ? 4 : nord); ++v) {
+    if (v > nord && v < 4) continue;
     // an order equal to an earlier one (a palindromic radix list) is not timed twice
     bool dup = false;
-    for (int u = 1; u < v && !dup; ++u) {
+    for (int u = 1; v <= 3 && u < v && !dup; ++u) {
       const FftPlanDev &a = P->xord[pi][u - 1], &b = P->xord[pi][v - 1];
       dup = a.npass == b.npass;
       for (int i = 0; dup && i < a.npass; ++i) dup = a.radix[i] == b.radix[i];
@@ -156,8 +159,9 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
     if (dup) continue;
     float ms = 0;
     VIE_TRY(time_ms(P->st, 3, [&] { return xpass<C>(P, spec, T, S, v, P->st); }, &ms));
-    const std::string name = v == 0 ? std::string(d.L == 2048 ? "radix16x16x8" : "radix16x16x16")
-                                    : radix_name(P->xord[pi][v - 1]);
+    const std::string name = v == 0   ? std::string(d.L == 2048 ? "radix16x16x8" : "radix16x16x16")
+                             : v == 4 ? std::string(d.L == 4096 ? "radix16x16x4x4" : "radix16x16x8x4")
+                                      : radix_name(P->xord[pi][v - 1]);
     snprintf(buf, sizeof(buf), " %s %.4f ms;", name.c_str(), ms);
     rep += buf;
     if (best < 0 || ms < tbest) { best = v; tbest = ms; }
@@ -226,3 +230,32 @@ vie_status tune_matvec(vie_plan_s* P) {
 }  // namespace vie
 
 extern "C" const char* vie_plan_tuning(vie_plan_t P) { return P ? P->tuning.c_str() : ""; }
+
+extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int choice) {
+  using namespace vie;
+  if (!P || !kernel) { set_error("vie_plan_set_tuning: NULL argument"); return VIE_EINVAL; }
+  const std::string k = kernel;
+  const MvDims& d = P->d;
+  if (k == "x_pass_c64" || k == "x_pass_c128") {
+    const bool c64 = k == "x_pass_c64";
+    const bool ok = choice == -1 || (choice >= 1 && choice <= 3) ||
+                    (c64 && choice == 0 && (d.L == 2048 || d.L == 4096)) ||
+                    (c64 && choice == 4 && (d.L == 4096 || d.L == 8192));
+    if (!ok) { set_error("vie_plan_set_tuning: x-pass variant %d does not exist for L = %d", choice, d.L); return VIE_EINVAL; }
+    P->xvar[c64 ? 0 : 1] = choice;
+  } else if (k == "yz_passes_c64") {
+    if (choice != 16 && choice != 8 && choice != 4) { set_error("vie_plan_set_tuning: yz columns must be 16, 8 or 4"); return VIE_EINVAL; }
+    P->yzxg = choice;
+  } else if (k == "block_gemv") {
+    if (choice != 1 && choice != 2 && choice != 4 && choice != 8) {
+      set_error("vie_plan_set_tuning: CTAs per block must be 1, 2, 4 or 8");
+      return VIE_EINVAL;
+    }
+    for (auto& B : P->bp) B->gemv_split = choice;
+  } else {
+    set_error("vie_plan_set_tuning: unknown kernel '%s'", kernel);
+    return VIE_EINVAL;
+  }
+  reset_graphs(P);   // captured steps hold the old launch shapes
+  return VIE_OK;
+}

@@ -85,6 +85,7 @@ _SIGS = {
                                          ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "vie_plan_tuning": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "vie_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]),
     "vie_last_error": (ctypes.c_char_p, []),
     "vie_kernel_launches": (ctypes.c_int64, []),
     "vie_profile_enable": (None, [ctypes.c_int]),
@@ -241,6 +242,11 @@ def vie_matvec_static(nx, ny, nz, h, k0, eps_bg, eps_ptr: int, x_ptr: int, y_ptr
 def vie_plan_tuning(plan) -> str:
     """The autotuner's report for the plan (candidates, times, choices)."""
     return (lib().vie_plan_tuning(plan) or b"").decode()
+
+
+def vie_plan_set_tuning(plan, kernel: str, choice: int) -> int:
+    """Override one autotuner choice (test hook); returns the status code."""
+    return lib().vie_plan_set_tuning(plan, kernel.encode(), choice)
 
 
 def vie_kernel_launches() -> int:

@@ -91,3 +91,62 @@ def test_yz_columns_per_cta_tuned_for_register_cross_sections():
     ref = op.fft_matvec(x, op.material(eps, 1.0),
                         op.generator_spectra(nx, ny, nz, 0.025, op.background_k(K0, 1.0)))
     assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("nx,variants", [(1013, [0, 1, 2, 3]), (2031, [0, 1, 2, 3, 4]), (4073, [1, 2, 3, 4]),
+                                         (700, [1, 2, 3])])
+def test_every_x_pass_variant_matches_oracle(nx, variants):
+    """Every candidate the tuner may choose, forced in turn through the test
+    hook: three-pass (L = 2048, 4096) and four-pass (L = 4096, 8192)
+    compile-time kernels and the generic kernel with each radix order, on
+    ragged lengths (zero padding and crop at non-aligned edges)."""
+    cuda_or_fail()
+    ny, nz = 3, 2
+    eps = inputs.random_permittivity(nz, ny, nx, seed=nx + 5)
+    x = inputs.random_field((3, nz, ny, nx), seed=nx + 6)
+    ref = op.fft_matvec(x, op.material(eps, 1.0),
+                        op.generator_spectra(nx, ny, nz, 0.025, op.background_k(K0, 1.0)))
+    plan = Plan(nx, ny, nz, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    plan.set_permittivity(eps)
+    xd = to_device(x)
+    for v in variants:
+        assert vie.vie_plan_set_tuning(plan.handle, "x_pass_c64", v) == vie.VIE_OK, (v, vie.last_error())
+        y = plan.matvec(xd, vie.VIE_MIXED).cpu().numpy()
+        assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6, (nx, v, relerr(y, ref))
+    for v in (1, 2, 3):
+        assert vie.vie_plan_set_tuning(plan.handle, "x_pass_c128", v) == vie.VIE_OK
+        y = plan.matvec(xd, vie.VIE_FP64).cpu().numpy()
+        assert maxerr(y, ref) <= 1e-12, (nx, v)
+    # a variant the shape does not have is refused
+    bad = 4 if nx in (1013, 700) else 0 if nx == 4073 else 5
+    assert vie.vie_plan_set_tuning(plan.handle, "x_pass_c64", bad) == vie.VIE_EINVAL
+    plan.close()
+
+
+def test_every_yz_and_gemv_choice_matches_oracle():
+    cuda_or_fail()
+    p = inputs.straight_guide(320, 16, 8, 0.025, 1.55)
+    M = op.material(p.eps, p.eps_bg)
+    k = op.background_k(p.k0, p.eps_bg)
+    x = inputs.random_field((3, p.nz, p.ny, p.nx), seed=41)
+    ref = op.fft_matvec(x, M, op.generator_spectra(p.nx, p.ny, p.nz, p.h, k))
+    from oracle import precond as pc
+    P = pc.Preconditioner(p.nx, p.ny, p.nz, p.h, k, M, p.boxes, 3, 1e-3)
+    zref = P.apply(x)
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, reduce_tol=1e-3)
+    plan.set_permittivity(p.eps)
+    plan.build()
+    xd = to_device(x)
+    for xg in (16, 8, 4):
+        assert vie.vie_plan_set_tuning(plan.handle, "yz_passes_c64", xg) == vie.VIE_OK
+        y = plan.matvec(xd, vie.VIE_MIXED).cpu().numpy()
+        assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6, xg
+    outs = []
+    for sp in (1, 2, 4, 8):
+        assert vie.vie_plan_set_tuning(plan.handle, "block_gemv", sp) == vie.VIE_OK
+        z = plan.precond(xd, vie.VIE_MIXED).cpu().numpy()
+        assert relerr(z, zref) <= 2e-6 and maxerr(z, zref) <= 2e-6, sp
+        outs.append(z)
+    for z in outs[1:]:   # the split does not change a single bit
+        np.testing.assert_array_equal(z, outs[0])
+    plan.close()
