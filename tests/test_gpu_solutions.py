@@ -80,3 +80,26 @@ def test_unpreconditioned_solve_matches_oracle():
         if precision == vie.VIE_FP64:
             # same Krylov method in FP64 (CGS2 on the GPU, MGS in the oracle)
             assert abs(info["iters_inner"] - orc.iters) <= 0.05 * orc.iters + 5, (info, orc.iters)
+
+
+@pytest.mark.parametrize("precision", [vie.VIE_MIXED, vie.VIE_FP64])
+def test_bragg_full_size_solution_matches_oracle_sample(precision):
+    """4096x24x8 Bragg grating (2.36 M unknowns, two x-boxes, real-mean
+    homogenised blocks, tau = 1e-3): the GPU solution at the benchmark
+    tolerance against a seeded sample of 4091 entries of the oracle's
+    solution (oracle GMRES to 1e-12, stored by make_oracle_solutions.py), in
+    norm and element-wise against the sample's largest entry."""
+    cuda_or_fail()
+    meta = json.load(open(os.path.join(GOLDEN, "oracle_solutions.json")))["bragg_4096x24x8_2boxes"]
+    assert meta["relres"] <= 1e-12
+    d = np.load(os.path.join(GOLDEN, meta["file"]))
+    idx, ref = d["idx"], d["w"]
+    p = inputs.workload_bragg()
+    plan = Plan.for_problem(p, precision=precision, tol=1e-9)
+    plan.set_permittivity(p.eps)
+    w, info = plan.solve(p.e_inc)
+    plan.close()
+    ws = w.cpu().numpy().ravel()[idx]
+    assert info["relres"] <= 1e-9
+    assert relerr(ws, ref) <= 1e-6, info
+    assert maxerr(ws, ref) <= 1e-6, info
