@@ -26,7 +26,8 @@
  * arrays, preconditioner blocks, Krylov workspace); it allocates device
  * memory in vie_plan_create, vie_build_preconditioner, the first vie_solve of
  * a plan (Krylov workspace), the first vie_solve_host of a plan (its three
- * staging buffers) and the vie_server_* calls, and never inside vie_matvec /
+ * staging buffers), the first FP64 fallback of a mixed solve (see
+ * vie_solve) and the vie_server_* calls, and never inside vie_matvec /
  * vie_precond_apply or later solves of the same plan.
  *
  * Streams: every call enqueues its GPU work on the stream given at plan
@@ -107,6 +108,11 @@ typedef struct {
   long long precond_discarded; /* frequencies applied with the representative block
                                   (the discarded ones, Sec. 5.1.1), over all boxes    */
   int reorth_passes;           /* Arnoldi steps that took the second Gram-Schmidt pass */
+  int iters_fp64_fallback;     /* mixed: GMRES iterations run in FP64 after the
+                                  refinement stalled (a correction that raised the
+                                  FP64 residual, or three steps under 1% gain); 0
+                                  when the complex-FP32 inner solves sufficed.
+                                  Included in iters_inner.                        */
 } vie_info;
 
 typedef struct vie_plan_s* vie_plan_t;
@@ -166,7 +172,12 @@ vie_status vie_precond_apply(vie_plan_t plan, const void* r_dev, void* z_dev, in
  * FP64 iterative refinement whose every step runs one complex-FP32 GMRES
  * cycle on the scaled FP64 residual (stopped early at the relative target
  * max(inner_tol, tol ||b|| / (2 ||r||))), so GMRES restarts from FP64
- * residuals.  e_inc and w_out are
+ * residuals.  When a correction raises the FP64 residual (it is taken back)
+ * or three steps in a row gain less than 1%, the solve goes on as FP64
+ * GMRES(restart) from its iterate: the first time, this builds the
+ * complex-FP64 inverses of the preconditioner and allocates the FP64 basis
+ * (as for VIE_FP64); info->iters_fp64_fallback counts those iterations.
+ * e_inc and w_out are
  * device [3][nz][ny][nx] double2.  Builds the preconditioner if needed.
  * info may be NULL.  Synchronises the plan stream. */
 vie_status vie_solve(vie_plan_t plan, const void* e_inc_dev, void* w_out_dev, vie_info* info);
@@ -253,8 +264,8 @@ vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double
 
 /* The autotuner's report for the plan: per tuned kernel the shape, each
  * candidate launch variant with its measured device time (ms) and the
- * choice -- the matvec's register yz passes (16, 8 or 4 x-columns per CTA)
- * and its x pass (compile-time radix-16 kernel or the generic Stockham
+ * choice -- the matvec's yz passes (x-columns per CTA of the register or of
+ * the generic kernels) and its x pass (compile-time radix-16 kernel or the generic Stockham
  * kernel with one of three radix orders, per precision), timed at plan
  * creation, and each box's kept-block product (1, 2, 4 or 8 CTAs per
  * block), timed at preconditioner build.  Choices are cached per process and
@@ -269,7 +280,9 @@ const char* vie_plan_tuning(vie_plan_t plan);
  * compile-time kernel, complex FP32, L = 2048 or 4096), 1..3 (generic
  * Stockham kernel with radix order 1..3) or 4 (four-pass compile-time kernel,
  * complex FP32, L = 4096 or 8192); "yz_passes_c64" with 16, 8 or 4 x-columns
- * per CTA; "block_gemv" with 1, 2, 4 or 8 CTAs per kept block (set on the
+ * per CTA of the register yz passes; "yz_generic_c64" with 1, 2, 4, 8 or 16
+ * x-columns per CTA of the generic yz passes (as shared memory allows);
+ * "block_gemv" with 1, 2, 4 or 8 CTAs per kept block (set on the
  * built preconditioner; a rebuild tunes again).  VIE_EINVAL for a variant that
  * does not exist for the plan's shape. */
 vie_status vie_plan_set_tuning(vie_plan_t plan, const char* kernel, int choice);

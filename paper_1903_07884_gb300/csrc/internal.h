@@ -69,7 +69,8 @@ struct BoxPrec {
   DevBuf zhat64, zhat128;
   DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
   DevBuf bpack, apack;       // tensor-core operands of the representative-block product (packed tf32 hi/lo)
-  int gemv_split = 0;        // kept-block product: CTAs per block (0: the default rule; set by the autotuner)
+  int gemv_split[2] = {0, 0};  // kept-block product: CTAs per block, complex FP32 / FP64 (0: the default
+                               // rule; set by the autotuner)
   const FftLen* fx = nullptr;
   // 2-level boxes: blocks of m2 = 3 nz rows for f <= n/2, g <= ny/2, slot
   // g * nfs + f, inverses column-major in inv64 / inv128; rhat/zhat [m2][ny][n]
@@ -101,6 +102,7 @@ struct vie_plan_s {
   int xvar[2] = {-1, -1};
   vie::FftPlanDev xord[2][3]{};
   int yzxg = 0;                        // x-columns per CTA of the register yz passes (0: 16)
+  int yzxg_gen = 0;                    // x-columns per CTA of the generic yz passes, complex FP32 (0: default rule)
   std::string tuning;                  // the autotuner's report (vie_plan_tuning)
   size_t tuning_matvec = 0;            // length of its matvec part (the rest belongs to the last build)
   vie::DevBuf spec128, spec64;         // [6][Pzh][Pyh][Lh] scaled generator spectra
@@ -145,6 +147,10 @@ vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStre
 // plan's staging buffers (autotuner timing); VIE_EINVAL if the cross-section
 // has no register variant
 vie_status yz_pair(vie_plan_s* P, int xg, cudaStream_t st);
+// both generic yz passes (complex FP32, shared-memory Stockham) with xg
+// x-columns per CTA on the plan's staging buffers; VIE_EINVAL if the plan
+// takes the register or the split-line passes, or xg columns do not fit
+vie_status yz_pair_generic(vie_plan_s* P, int xg, cudaStream_t st);
 
 // tune.cu: per-shape choice among launch variants, by timing on the plan's
 // own buffers (cached per process and shape)
@@ -184,6 +190,7 @@ vie_status precond_build(vie_plan_s* P);
 template <class C>
 vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st);
 void precond_free(vie_plan_s* P);
+vie_status precond_add_fp64(vie_plan_s* P);
 vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plane);
 vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
                                 DevBuf* inv128);

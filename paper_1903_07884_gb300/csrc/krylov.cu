@@ -992,11 +992,11 @@ __global__ void k_combine(const C* __restrict__ V, long long ld, C* __restrict__
   }
 }
 
-// x += scale * z   (x FP64, z any precision)
+// x += sgn * scale * z   (x FP64, z any precision)
 template <class C>
 __global__ void k_axpy_to64(double2* __restrict__ x, const C* __restrict__ z, long long n3, const double* __restrict__ sc,
-                            int sidx) {
-  const double a = sc ? sc[sidx] : 1.0;
+                            int sidx, double sgn) {
+  const double a = sgn * (sc ? sc[sidx] : 1.0);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
     x[e].x += a * (double)z[e].x;
     x[e].y += a * (double)z[e].y;
@@ -1252,6 +1252,9 @@ struct Run {
   // FP64 iterative refinement of a mixed solve
   double rn = 0, rn_prev = 0;
   int ir_stalls = 0;
+  // the mixed solve fell back to FP64 GMRES (its iterations in that run)
+  bool fallback = false;
+  int fallback_iters = 0;
   // the GMRES run in progress (complex FP32 inner cycle, or the FP64 solve)
   double gnorm = 0, gtol = 0;
   int gmax_iter = 0, gmax_cycles = 0, gtotal = 0, gcycles = 0, gstalls = 0;
@@ -1316,9 +1319,48 @@ static vie_status gmres_done(Run& R);
 
 template <>
 vie_status gmres_done<double2>(Run& R) {
-  R.inner = R.gtotal;
-  R.outer = 1;
+  if (R.fallback) {
+    R.fallback_iters = R.gtotal;
+    R.inner += R.gtotal;
+    ++R.outer;
+  } else {
+    R.inner = R.gtotal;
+    R.outer = 1;
+  }
   return run_finish(R);
+}
+
+// A mixed solve whose refinement stopped making progress goes on as FP64
+// GMRES(restart) from its current iterate, with the complex-FP64 inverses of
+// the same preconditioner.  The complex-FP32 inner solve fails when the
+// operator or a preconditioner block is too ill-conditioned for FP32
+// (a correction that raises the FP64 residual, or steps that gain less than
+// 1%); FP64 GMRES then converges as the FP64 solve of the same system does.
+static vie_status fallback_fp64(Run& R) {
+  vie_plan_s* P = R.P;
+  if (R.rn <= P->opts.tol * R.bnorm || R.inner >= P->opts.max_iter) return run_finish(R);
+  {
+    AllocScope a(P->st);
+    VIE_TRY(krylov_alloc(P, true, true));
+    VIE_TRY(precond_add_fp64(P));
+  }
+  Krylov& K = *P->kry;
+  R.mixed = false;
+  R.fallback = true;
+  // r128 = b - A x of the current iterate; A x = b from x (the best iterate
+  // so far, kept in xbest)
+  R.gnorm = R.bnorm;
+  R.gtol = P->opts.tol;
+  R.gmax_iter = P->opts.max_iter - R.inner;
+  R.gmax_cycles = 1 << 30;
+  R.gtotal = 0;
+  R.gcycles = 0;
+  R.gstalls = 0;
+  R.rr = R.rn / R.bnorm;
+  R.rr_best = R.rr;
+  VIE_CUDA(cudaMemcpyAsync(K.xbest.p, K.x128.p, sizeof(double2) * K.n3, cudaMemcpyDeviceToDevice, P->st));
+  R.have_best = true;
+  return cycle_begin<double2>(R);
 }
 
 template <>
@@ -1332,14 +1374,17 @@ vie_status gmres_done<float2>(Run& R) {
   double2* x = K.x128.as<double2>();
   double2* r = K.r128.as<double2>();
   double2* t = K.t128.as<double2>();
-  k_axpy_to64<float2><<<grid_for(n3), 256, 0, st>>>(x, K.d64.as<float2>(), n3, K.scal.as<double>(), 3);
+  double* scal = K.scal.as<double>();
+  // x += ||r|| d (scal[3] = ||r|| of the step's right-hand side)
+  k_axpy_to64<float2><<<grid_for(n3), 256, 0, st>>>(x, K.d64.as<float2>(), n3, scal, 3, 1.0);
   count_launch();
   VIE_TRY(op_A<double2>(P, x, t));
   k_sub<<<grid_for(n3), 256, 0, st>>>(K.b128.as<double2>(), t, r, n3);
   count_launch();
   VIE_CHECK_LAUNCH();
   ++R.outer;
-  VIE_TRY(norm128(P, r, 3, &R.rn));
+  const double rn_step = R.rn;
+  VIE_TRY(norm128(P, r, 5, &R.rn));
   if (!std::isfinite(R.rn)) {
     int herr = 0;
     VIE_CUDA(cudaMemcpyAsync(&herr, P->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1351,13 +1396,26 @@ vie_status gmres_done<float2>(Run& R) {
     set_error("vie_solve: refinement diverged (non-finite residual)");
     return VIE_ECUDA;
   }
+  if (R.rn > rn_step && it > 0) {
+    // the correction raised the FP64 residual: take it back (x -= ||r|| d,
+    // scal[3] still holds ||r||) and go on in FP64
+    k_axpy_to64<float2><<<grid_for(n3), 256, 0, st>>>(x, K.d64.as<float2>(), n3, scal, 3, -1.0);
+    count_launch();
+    VIE_TRY(op_A<double2>(P, x, t));
+    k_sub<<<grid_for(n3), 256, 0, st>>>(K.b128.as<double2>(), t, r, n3);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    VIE_TRY(norm128(P, r, 3, &R.rn));
+    return fallback_fp64(R);
+  }
+  VIE_CUDA(cudaMemcpyAsync(scal + 3, scal + 5, sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (it == 0) return run_finish(R);
   // three refinement steps in a row that do not reduce the FP64 residual by
-  // 1% mean the inner solve has nothing left to give (the rule of the FP64
-  // GMRES restarts; a hard operator may gain only a few percent per cycle
-  // and still converge)
+  // 1% mean the complex-FP32 inner solve has nothing left to give (the rule
+  // of the FP64 GMRES restarts; a hard operator may gain only a few percent
+  // per cycle and still converge)
   if (R.rn > 0.99 * R.rn_prev) {
-    if (++R.ir_stalls >= 3) return run_finish(R);
+    if (++R.ir_stalls >= 3) return fallback_fp64(R);
   } else {
     R.ir_stalls = 0;
   }
@@ -1534,6 +1592,7 @@ static vie_status run_finish(Run& R) {
     info->precond_blocks = P->precond_blocks;
     info->precond_discarded = P->precond_discarded;
     info->reorth_passes = hreorth;
+    info->iters_fp64_fallback = R.fallback_iters;
   }
   R.finished = true;
   R.status = relres <= P->opts.tol ? VIE_OK : VIE_ENOCONV;
@@ -1606,6 +1665,7 @@ struct Lockstep {
   int* done_host = nullptr;                   // pinned mirror
   cudaGraphExec_t exec = nullptr;
   std::vector<Run*> members;                  // the set the graph was captured for
+  std::vector<char> modes;                    // and each member's precision then (1 = mixed)
   int nd64 = 0, ncta64 = 0, nd128 = 0, ncta128 = 0;   // work-lists of the captured set
   int step_launches = 0;
   ~Lockstep() { release(); }
@@ -1616,6 +1676,7 @@ struct Lockstep {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
     members.clear();
+    modes.clear();
     for (auto s : br) cudaStreamDestroy(s);
     for (auto e : ev_br) cudaEventDestroy(e);
     br.clear();
@@ -1742,7 +1803,10 @@ static bool lockstep_pass_impl(Lockstep& L, std::vector<Run*>& runs, cudaStream_
       if (!R->finished && R->in_cycle) m.push_back(R);
     if (m.empty()) return false;
     vie_status s = lockstep_init(L, (int)m.size());
-    if (s >= 0 && m != L.members) {
+    std::vector<char> md;
+    for (Run* R : m) md.push_back(R->mixed ? 1 : 0);
+    // a mixed run that fell back to FP64 changes its step kernels
+    if (s >= 0 && (m != L.members || md != L.modes)) {
       // (re)capture the step graph for this set
       if (L.exec) { cudaGraphExecDestroy(L.exec); L.exec = nullptr; }
       L.members.clear();
@@ -1780,7 +1844,10 @@ static bool lockstep_pass_impl(Lockstep& L, std::vector<Run*>& runs, cudaStream_
           if (ce == cudaSuccess) cudaGraphDestroy(graph);
         }
       }
-      if (s >= 0) L.members = m;
+      if (s >= 0) {
+        L.members = m;
+        L.modes = md;
+      }
     }
     if (s < 0) {
       for (Run* R : m) run_fail(*R, s);

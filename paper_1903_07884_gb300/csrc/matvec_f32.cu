@@ -16,4 +16,23 @@ vie_status yz_pair(vie_plan_s* P, int xg, cudaStream_t st) {
   // (the staging vector stands in for M: only the timing matters here)
   return yz_r_launch(P->d, yzr, xg, false, nullptr, nullptr, T, x, y, st, x);
 }
+
+vie_status yz_pair_generic(vie_plan_s* P, int xg, cudaStream_t st) {
+  const MvDims& d = P->d;
+  if (yz_variant(d) || P->yz_split) return VIE_EINVAL;
+  const size_t smem = 2 * (size_t)xg * (d.Py * d.Pz + 1) * sizeof(float2);
+  if (smem > 200 * 1024) return VIE_EINVAL;
+  const FftPlanDev py = planof<float2>(*P->fPy), pz = planof<float2>(*P->fPz);
+  float2* x = P->xin64.as<float2>();
+  float2* y = P->xout64.as<float2>();
+  float2* T = P->T64.as<float2>();
+  const dim3 g(ceil_div(d.nx, xg), 3);
+  VIE_TRY(set_smem(k_mv_yz_fwd<float2>, smem));
+  VIE_TRY(set_smem(k_mv_yz_inv<float2>, smem));
+  k_mv_yz_fwd<float2><<<g, 256, smem, st>>>(x, T, d, py, pz, xg);
+  // (the staging vector stands in for M: only the timing matters here)
+  k_mv_yz_inv<float2><<<g, 256, smem, st>>>(T, x, x, y, d, py, pz, xg);
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
 }  // namespace vie

@@ -944,7 +944,9 @@ vie_status matvec(vie_plan_s* P, const C* x, C* y, const C* Mv, const C* spec, C
   const MvDims& d = P->d;
   const int cap = 16;
   // pass A
-  const int XG = pick_xg(d, sizeof(C));
+  // x-columns per CTA of the generic yz passes: the autotuner's choice
+  // (complex FP32), else the rule of pick_xg
+  const int XG = (sizeof(C) == 8 && P->yzxg_gen > 0) ? std::min(P->yzxg_gen, std::max(1, d.nx)) : pick_xg(d, sizeof(C));
   const size_t smemA = 2 * (size_t)XG * (d.Py * d.Pz + 1) * sizeof(C);
   dim3 gA(ceil_div(d.nx, XG), 3);
   const FftPlanDev py = planof<C>(*P->fPy), pz = planof<C>(*P->fPz), pl = planof<C>(*P->fL);

@@ -1042,13 +1042,14 @@ vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool
     k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
                                                                                         LU32.as<float2>(), tot);
     count_launch();
-    if (m <= 8 * 48) {
+    if (m <= 8 * 72) {
       // register-blocked: 8 row groups x 32 columns per CTA
       dim3 gr(nblk, ceil_div(m, 32));
       Prof pf_("block_inv_c64", st);
       if (m <= 8 * 16) k_block_inv_rb<16><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
       else if (m <= 8 * 32) k_block_inv_rb<32><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
-      else k_block_inv_rb<48><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
+      else if (m <= 8 * 48) k_block_inv_rb<48><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
+      else k_block_inv_rb<72><<<gr, 256, 0, st>>>(LU32.as<float2>(), piv.as<int>(), inv64->as<float2>(), m);
     } else {
       const size_t smem = sizeof(float2) * (size_t)m * (CB + 3);
       VIE_TRY(smem_optin(k_block_inv<float2>, smem));
@@ -1123,7 +1124,7 @@ static vie_status tune_gemv(vie_plan_s* P, BoxPrec& B, int pi) {
     choice = best;
     tune_cache_put(key, choice, rep);
   }
-  B.gemv_split = choice;
+  B.gemv_split[pi] = choice;
   P->tuning += rep;
   return VIE_OK;
 }
@@ -1259,6 +1260,25 @@ vie_status precond_build(vie_plan_s* P) {
   return VIE_OK;
 }
 
+// The complex-FP64 inverses of a preconditioner built for the mixed solve
+// (its blocks are rebuilt in the same order, so the selection and the
+// complex-FP32 inverses stay as they are): used when a mixed solve falls
+// back to FP64 GMRES.
+vie_status precond_add_fp64(vie_plan_s* P) {
+  if (!P->prec_built) { set_error("preconditioner not built"); return VIE_ESTATE; }
+  size_t bytes = 0;
+  for (auto& Bp : P->bp) {
+    BoxPrec& B = *Bp;
+    if (!B.inv128.p) {
+      if (B.b.levels == 2) VIE_TRY(build_box2(P, B, false, true));
+      else VIE_TRY(build_box(P, B, false, true));
+    }
+    bytes += B.inv64.bytes + B.inv128.bytes + B.bpack.bytes + B.apack.bytes;
+  }
+  P->precond_bytes = bytes;
+  return VIE_OK;
+}
+
 template <class C> struct BoxBufs;
 template <> struct BoxBufs<float2> {
   static float2* inv(BoxPrec& B) { return B.inv64.as<float2>(); }
@@ -1325,7 +1345,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
         VIE_CHECK_LAUNCH();
       }
     }
-    if (B.nhalf > 0) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, B.gemv_split, st));
+    if (B.nhalf > 0) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, B.gemv_split[sizeof(C) == 16], st));
     if (tc) {
       VIE_CUDA(cudaEventRecord(P->ev_join, P->side));
       VIE_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));

@@ -1,8 +1,9 @@
 // Autotuner.  For the shapes of a plan it times the candidate launch variants
 // of three kernels on the plan's own buffers and keeps the fastest:
-//   * the matvec's register yz passes (complex FP32, power-of-two
-//     cross-sections): 16, 8 or 4 x-columns per CTA (every choice transforms
-//     the same columns the same way, so results do not depend on it);
+//   * the matvec's yz passes (complex FP32): 16, 8 or 4 x-columns per CTA of
+//     the register kernels (power-of-two cross-sections), 1 to 16 of the
+//     generic shared-memory kernels otherwise (every choice transforms the
+//     same columns the same way, so results do not depend on it);
 //   * the matvec's x pass (per precision): the compile-time kernels where
 //     they exist (complex FP32: three passes 16x16x8 for L = 2048, 16x16x16
 //     for 4096; four passes 16x16x4x4 for 4096, 16x16x8x4 for 8192) and the
@@ -176,11 +177,13 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
 
 // x-columns per CTA of the register yz passes (forward and inverse timed
 // together; every choice transforms the same columns the same way)
+static vie_status tune_yz_generic(vie_plan_s* P);
+
 static vie_status tune_yz(vie_plan_s* P) {
   const MvDims& d = P->d;
   if (yz_pair(P, 16, P->st) == VIE_EINVAL) {
     cudaGetLastError();
-    return VIE_OK;
+    return tune_yz_generic(P);
   }
   const TuneKey key{2, 0, d.Py, d.Pz, d.nx * 64 + d.nz};
   int choice;
@@ -206,6 +209,45 @@ static vie_status tune_yz(vie_plan_s* P) {
     tune_cache_put(key, choice, rep);
   }
   P->yzxg = choice;
+  P->tuning += rep;
+  return VIE_OK;
+}
+
+// x-columns per CTA of the generic (shared-memory Stockham) yz passes, for
+// cross-sections without a register variant: 1, 2, 4, 8, 16 as shared memory
+// allows (each column is transformed the same way whatever the grouping)
+static vie_status tune_yz_generic(vie_plan_s* P) {
+  const MvDims& d = P->d;
+  if (yz_pair_generic(P, 1, P->st) == VIE_EINVAL) {
+    cudaGetLastError();
+    return VIE_OK;
+  }
+  const TuneKey key{3, 0, d.Py, d.Pz, d.nx * 64 + d.nz};
+  int choice;
+  std::string rep;
+  if (!tune_cache_get(key, &choice, &rep)) {
+    const long long n3 = 3LL * d.nx * d.ny * d.nz;
+    VIE_CUDA(cudaMemsetAsync(P->xin64.p, 0, sizeof(float2) * n3, P->st));
+    char buf[160];
+    snprintf(buf, sizeof(buf), "yz_generic_c64 nx=%d Py=%d Pz=%d nz=%d:", d.nx, d.Py, d.Pz, d.nz);
+    rep = buf;
+    int best = 0;
+    float tbest = 0;
+    for (int xg : {1, 2, 4, 8, 16}) {
+      if (xg > std::max(1, d.nx)) break;
+      if (2 * (size_t)xg * (d.Py * d.Pz + 1) * sizeof(float2) > 200 * 1024) break;
+      float ms = 0;
+      VIE_TRY(time_ms(P->st, 3, [&] { return yz_pair_generic(P, xg, P->st); }, &ms));
+      snprintf(buf, sizeof(buf), " %d columns/CTA %.4f ms;", xg, ms);
+      rep += buf;
+      if (best == 0 || ms < tbest) { best = xg; tbest = ms; }
+    }
+    snprintf(buf, sizeof(buf), " chosen %d\n", best);
+    rep += buf;
+    choice = best;
+    tune_cache_put(key, choice, rep);
+  }
+  P->yzxg_gen = choice;
   P->tuning += rep;
   return VIE_OK;
 }
@@ -243,6 +285,13 @@ extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int 
                     (c64 && choice == 4 && (d.L == 4096 || d.L == 8192));
     if (!ok) { set_error("vie_plan_set_tuning: x-pass variant %d does not exist for L = %d", choice, d.L); return VIE_EINVAL; }
     P->xvar[c64 ? 0 : 1] = choice;
+  } else if (k == "yz_generic_c64") {
+    if (choice < 1 || choice > 16 || (choice & (choice - 1)) ||
+        2 * (size_t)choice * (d.Py * d.Pz + 1) * sizeof(float2) > 200 * 1024) {
+      set_error("vie_plan_set_tuning: generic yz columns must be 1..16 (power of two, fitting shared memory)");
+      return VIE_EINVAL;
+    }
+    P->yzxg_gen = choice;
   } else if (k == "yz_passes_c64") {
     if (choice != 16 && choice != 8 && choice != 4) { set_error("vie_plan_set_tuning: yz columns must be 16, 8 or 4"); return VIE_EINVAL; }
     P->yzxg = choice;
@@ -251,7 +300,7 @@ extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int 
       set_error("vie_plan_set_tuning: CTAs per block must be 1, 2, 4 or 8");
       return VIE_EINVAL;
     }
-    for (auto& B : P->bp) B->gemv_split = choice;
+    for (auto& B : P->bp) B->gemv_split[P->opts.precision == VIE_FP64] = choice;
   } else {
     set_error("vie_plan_set_tuning: unknown kernel '%s'", kernel);
     return VIE_EINVAL;

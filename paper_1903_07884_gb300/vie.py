@@ -40,7 +40,8 @@ class vie_info(ctypes.Structure):
                 ("relres", ctypes.c_double), ("precond_bytes", ctypes.c_size_t),
                 ("kept_fraction", ctypes.c_double), ("t_setup_ms", ctypes.c_float),
                 ("t_solve_ms", ctypes.c_float), ("precond_blocks", ctypes.c_longlong),
-                ("precond_discarded", ctypes.c_longlong), ("reorth_passes", ctypes.c_int)]
+                ("precond_discarded", ctypes.c_longlong), ("reorth_passes", ctypes.c_int),
+                ("iters_fp64_fallback", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

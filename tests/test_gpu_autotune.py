@@ -150,3 +150,33 @@ def test_every_yz_and_gemv_choice_matches_oracle():
     for z in outs[1:]:   # the split does not change a single bit
         np.testing.assert_array_equal(z, outs[0])
     plan.close()
+
+
+def test_generic_yz_columns_tuned_and_every_choice_matches_oracle():
+    """A 24x4-voxel cross-section (Py = 48, Pz = 8) has no register yz kernel:
+    the tuner times 1..16 x-columns per CTA of the generic shared-memory
+    passes; every choice gives bitwise the same matvec, within 1e-6 of the
+    oracle."""
+    cuda_or_fail()
+    nx, ny, nz = 96, 24, 4
+    plan = Plan(nx, ny, nz, 0.025, K0, 2.085, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    rep = vie.vie_plan_tuning(plan.handle)
+    lines = _xpass_lines(rep, "yz_generic_c64")
+    assert len(lines) == 1, rep
+    cols = [int(c) for c, _ in re.findall(r" (\d+) columns/CTA ([0-9.]+) ms;", lines[0])]
+    assert cols[:3] == [1, 2, 4], lines[0]
+    eps = inputs.random_permittivity(nz, ny, nx, seed=19)
+    x = inputs.random_field((3, nz, ny, nx), seed=20)
+    plan.set_permittivity(eps)
+    ref = op.fft_matvec(x, op.material(eps, 2.085),
+                        op.generator_spectra(nx, ny, nz, 0.025, op.background_k(K0, 2.085)))
+    xd = to_device(x)
+    outs = []
+    for xg in cols:
+        assert vie.vie_plan_set_tuning(plan.handle, "yz_generic_c64", xg) == vie.VIE_OK
+        y = plan.matvec(xd, vie.VIE_MIXED).cpu().numpy()
+        assert relerr(y, ref) <= 1e-6 and maxerr(y, ref) <= 1e-6, xg
+        outs.append(y)
+    for y in outs[1:]:
+        np.testing.assert_array_equal(y, outs[0])
+    plan.close()

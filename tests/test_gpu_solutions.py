@@ -103,3 +103,26 @@ def test_bragg_full_size_solution_matches_oracle_sample(precision):
     assert info["relres"] <= 1e-9
     assert relerr(ws, ref) <= 1e-6, info
     assert maxerr(ws, ref) <= 1e-6, info
+
+
+@pytest.mark.parametrize("precision", [vie.VIE_MIXED, vie.VIE_FP64])
+def test_coupler_full_size_solution_matches_oracle_sample(precision):
+    """2048x48x8 directional coupler (two 16-wide cores, two x-boxes) at the
+    first wavelength of its sweep, 1.50 um: the GPU solution at the benchmark
+    tolerance against a seeded sample of the oracle's solution (oracle GMRES
+    to 1e-12, stored by make_oracle_solutions.py)."""
+    cuda_or_fail()
+    name = "coupler_2048x48x8_2boxes_lambda1.50"
+    meta = json.load(open(os.path.join(GOLDEN, "oracle_solutions.json")))[name]
+    assert meta["relres"] <= 1e-12
+    d = np.load(os.path.join(GOLDEN, meta["file"]))
+    idx, ref = d["idx"], d["w"]
+    p = inputs.workload_coupler(wavelength=1.50)
+    plan = Plan.for_problem(p, precision=precision, tol=1e-9)
+    plan.set_permittivity(p.eps)
+    w, info = plan.solve(p.e_inc)
+    plan.close()
+    ws = w.cpu().numpy().ravel()[idx]
+    assert info["relres"] <= 1e-9
+    assert relerr(ws, ref) <= 1e-6, info
+    assert maxerr(ws, ref) <= 1e-6, info
