@@ -161,9 +161,10 @@ def algorithmic(kernel: str, p, plan_meta: dict):
     if kernel == "rep_gemm_tc":
         m, nd = plan_meta["m"], plan_meta["ndisc"]
         return "tensor", 8.0 * nd * m * m              # nd x m x m complex multiply-adds
-    if kernel == "lu_update":
+    if kernel in ("lu_update", "lu_update_c64"):
         # trailing updates A22 -= L21 U12 of the blocked LU (panels of 16): 8 real flops per
-        # complex multiply-add, averaged over the panel steps (one launch per step and box)
+        # complex multiply-add, averaged over the panel steps (one launch per step and box);
+        # complex FP64 for the FP64 preconditioner, complex FP32 for the mixed one
         m, nblk = plan_meta["m"], plan_meta["nblk"]
         steps = [(k0, min(16, m - k0)) for k0 in range(0, m, 16) if m - k0 - min(16, m - k0) > 0]
         flops = sum(8.0 * nb * (m - k0 - nb) ** 2 for k0, nb in steps)
@@ -494,10 +495,13 @@ def run_gpu(args):
                                    "issues 3 MMAs per algorithmic product)"}
         else:
             ach = amount / (avg_ms * 1e-3) / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": tot / total_prof,
+            f32 = name.endswith("_c64")
+            alu = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s",
+                    "frac": ach / alu, "traffic": None, "share": tot / total_prof,
                     "avg_launch_ms": avg_ms, "launches": cnt,
-                    "peak_source": "FP64 FMA probe (8 independent DFMA chains x 8 warps x 152 SMs)"}
+                    "peak_source": ("FP32 FMA probe (8 independent FFMA chains" if f32 else
+                                    "FP64 FMA probe (8 independent DFMA chains") + " x 8 warps x 152 SMs)"}
         break
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -151,8 +151,9 @@ vie_status vie_set_permittivity(vie_plan_t plan, const void* eps_dev);
  * per box, homogenise M (Sec. 5.2), form the Chan eigenvalues (Eq. Chan and
  * the diagonalisation C = F^-1 Lambda F), assemble the per-frequency blocks
  * D_f (Eq. Di), select the kept blocks (Eqs. proxy1-proxy2) when
- * reduce_tol > 0, and factor every kept block by FP64 LU with partial
- * pivoting; the inverse is stored in complex FP32 (mixed) and/or FP64.
+ * reduce_tol > 0, and factor every kept block by LU with partial pivoting
+ * (complex FP64 for VIE_FP64; complex FP32, from the FP64-assembled blocks,
+ * for VIE_MIXED); the explicit inverse is stored in the solve's precision.
  * Synchronises the plan stream.  No-op for VIE_PREC_NONE. */
 vie_status vie_build_preconditioner(vie_plan_t plan);
 

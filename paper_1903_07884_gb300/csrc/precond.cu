@@ -285,25 +285,30 @@ __global__ void k_block_assemble(double2* __restrict__ D, const double2* __restr
 }
 
 // ---------------------------------------------------------------------------
-// 5a. batched FP64 LU with partial pivoting (column-major, right-looking with
-//     panels of NB columns).  Each panel step is two launches over all
-//     matrices: the panel (pivoting, row swaps, U12 = L11^-1 A12; one block per
-//     matrix), then the trailing update A22 -= L21 U12 as 32x32 tiles of every
-//     matrix, so that the FP64 work fills every SM whatever the batch size.
+// 5a. batched LU with partial pivoting (column-major, right-looking with
+//     panels of NB columns), in complex FP64 for the FP64 preconditioner and
+//     in complex FP32 for the complex-FP32 one.  Each panel step is two
+//     launches over all matrices: the panel (pivoting, row swaps,
+//     U12 = L11^-1 A12; one block per matrix), then the trailing update
+//     A22 -= L21 U12 as 32x32 tiles of every matrix, so that the work fills
+//     every SM whatever the batch size.
 // ---------------------------------------------------------------------------
 constexpr int LU_NB = 16;
 constexpr int LU_TILE = 32;
 
-__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+template <class C>
+__device__ __forceinline__ typename real_of<C>::type cabs1(C a) { return fabs(a.x) + fabs(a.y); }
 
-__global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, int* __restrict__ pivall, int m,
-                                                  int k0, int* __restrict__ info) {
+template <class C>
+__global__ void __launch_bounds__(512) k_lu_panel(C* __restrict__ Aall, int* __restrict__ pivall, int m, int k0,
+                                                  int* __restrict__ info) {
+  using R = typename real_of<C>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* P = reinterpret_cast<double2*>(smem_raw);     // panel: NB columns x (m - k0) rows
-  __shared__ double rv[32];
+  C* P = reinterpret_cast<C*>(smem_raw);     // panel: NB columns x (m - k0) rows
+  __shared__ R rv[32];
   __shared__ int ri[32];
   __shared__ int piv_s;
-  double2* A = Aall + (long long)blockIdx.x * m * m;
+  C* A = Aall + (long long)blockIdx.x * m * m;
   int* piv = pivall + (long long)blockIdx.x * m;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -316,45 +321,49 @@ __global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, in
   __syncthreads();
   for (int kk = 0; kk < nb; ++kk) {
     const int k = k0 + kk;
-    double2* col = P + kk * rows;
+    C* col = P + kk * rows;
     // pivot search over rows k..m-1 (first maximum of |re| + |im|); the
     // candidate starts at the diagonal row so that the index stays valid
     // even if every entry compares false (NaN)
-    double best = -1.0;
+    R best = -1;
     int bi = kk;
     for (int i = kk + tid; i < rows; i += nt) {
-      const double v = cabs1(col[i]);
+      const R v = cabs1(col[i]);
       if (v > best) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const R ov = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
     if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
-      double b0 = rv[0];
+      R b0 = rv[0];
       int i0 = ri[0];
       for (int w = 1; w < nw; ++w)
         if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
       if (i0 < kk || i0 >= rows) i0 = kk;
       piv_s = i0;
       piv[k] = k0 + i0;
-      if (!(b0 > 0.0)) atomicExch(info, 1);   // zero or non-finite pivot
+      if (!(b0 > 0)) atomicExch(info, 1);   // zero or non-finite pivot
     }
     __syncthreads();
     const int pi = piv_s;
     if (pi != kk) {   // swap rows kk and pi inside the panel
       for (int j = tid; j < nb; j += nt) {
-        const double2 t = P[j * rows + kk];
+        const C t = P[j * rows + kk];
         P[j * rows + kk] = P[j * rows + pi];
         P[j * rows + pi] = t;
       }
     }
     __syncthreads();
-    const double2 pv = col[kk];
-    const double2 ipv = (pv.x == 0.0 && pv.y == 0.0) ? make_double2(0, 0) : cinv(pv);
+    const C pv = col[kk];
+    C ipv = czero<C>();
+    if (pv.x != 0 || pv.y != 0) {
+      const R d = R(1) / (pv.x * pv.x + pv.y * pv.y);
+      ipv = cmake<C>(pv.x * d, -pv.y * d);
+    }
     for (int i = kk + 1 + tid; i < rows; i += nt) col[i] = cmul(col[i], ipv);
     __syncthreads();
     // rank-1 update of the remaining panel columns
@@ -362,8 +371,8 @@ __global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, in
     for (int e = tid; e < rem * (rows - kk - 1); e += nt) {
       const int jj = kk + 1 + e / (rows - kk - 1);
       const int i = kk + 1 + e % (rows - kk - 1);
-      double2 a = P[jj * rows + i];
-      const double2 l = col[i], u = P[jj * rows + kk];
+      C a = P[jj * rows + i];
+      const C l = col[i], u = P[jj * rows + kk];
       a.x -= l.x * u.x - l.y * u.y;
       a.y -= l.x * u.y + l.y * u.x;
       P[jj * rows + i] = a;
@@ -378,22 +387,22 @@ __global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, in
   // the columns still to be factored), then U12 = L11^{-1} A12
   for (int j = tid; j < m; j += nt) {
     if (j >= k0 && j < k0 + nb) continue;
-    double2* cj = A + (long long)j * m;
+    C* cj = A + (long long)j * m;
     for (int kk = 0; kk < nb; ++kk) {
       const int k = k0 + kk, p = piv[k];
-      if (p != k) { const double2 t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
+      if (p != k) { const C t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
     }
     if (j >= k0 + nb) {
-      double2 u[LU_NB];
+      C u[LU_NB];
 #pragma unroll
-      for (int t = 0; t < LU_NB; ++t) u[t] = t < nb ? cj[k0 + t] : make_double2(0, 0);
+      for (int t = 0; t < LU_NB; ++t) u[t] = t < nb ? cj[k0 + t] : czero<C>();
 #pragma unroll
       for (int t = 0; t < LU_NB; ++t) {
         if (t >= nb) break;
 #pragma unroll
         for (int i = t + 1; i < LU_NB; ++i) {
           if (i >= nb) break;
-          const double2 l = P[t * rows + i];
+          const C l = P[t * rows + i];
           u[i].x -= l.x * u[t].x - l.y * u[t].y;
           u[i].y -= l.x * u[t].y + l.y * u[t].x;
         }
@@ -404,46 +413,67 @@ __global__ void __launch_bounds__(512) k_lu_panel(double2* __restrict__ Aall, in
   }
 }
 
-// A22 -= L21 U12 on one 32x32 tile of one matrix, with three real products
-// per complex product (T1 = Lr Ur, T2 = Li Ui, T3 = (Lr + Li)(Ur + Ui);
-// re -= T1 - T2, im -= T3 - T1 - T2): FP64 issues slowly on this part, and
-// this saves a quarter of the multiply-adds.  Thread (tx, ty) owns rows
-// tx, tx + 16 and columns ty, ty + 16 of the tile.
-__global__ void __launch_bounds__(256) k_lu_update(double2* __restrict__ Aall, int m, int k0, int nb) {
-  __shared__ double Lr[LU_NB][LU_TILE], Li[LU_NB][LU_TILE], Ls[LU_NB][LU_TILE];
-  __shared__ double Ur[LU_NB][LU_TILE], Ui[LU_NB][LU_TILE], Us[LU_NB][LU_TILE];
+// A22 -= L21 U12 on one 32x32 tile of one matrix.  Thread (tx, ty) owns
+// rows tx, tx + 16 and columns ty, ty + 16 of the tile.  Complex FP64 takes
+// three real products per complex product (T1 = Lr Ur, T2 = Li Ui,
+// T3 = (Lr + Li)(Ur + Ui); re -= T1 - T2, im -= T3 - T1 - T2): FP64 issues
+// slowly on this part, and this saves a quarter of the multiply-adds.
+// Complex FP32 keeps the four products (no cancellation in T3 - T1 - T2).
+template <class C>
+__global__ void __launch_bounds__(256) k_lu_update(C* __restrict__ Aall, int m, int k0, int nb) {
+  using R = typename real_of<C>::type;
+  constexpr bool k3m = sizeof(R) == 8;
+  __shared__ R Lr[LU_NB][LU_TILE], Li[LU_NB][LU_TILE], Ls[k3m ? LU_NB : 1][LU_TILE];
+  __shared__ R Ur[LU_NB][LU_TILE], Ui[LU_NB][LU_TILE], Us[k3m ? LU_NB : 1][LU_TILE];
   const int r0 = k0 + nb;                    // first row / column of A22
   const int r22 = m - r0;
   const int nti = (r22 + LU_TILE - 1) / LU_TILE;
   const int i0 = r0 + (blockIdx.x % nti) * LU_TILE, j0 = r0 + (blockIdx.x / nti) * LU_TILE;
-  double2* A = Aall + (long long)blockIdx.y * m * m;
+  C* A = Aall + (long long)blockIdx.y * m * m;
   const int tid = threadIdx.x;
   for (int e = tid; e < LU_NB * LU_TILE; e += blockDim.x) {
     const int t = e / LU_TILE, q = e % LU_TILE;
-    double2 l = make_double2(0, 0), u = make_double2(0, 0);
+    C l = czero<C>(), u = czero<C>();
     if (t < nb && i0 + q < m) l = A[(long long)(k0 + t) * m + i0 + q];   // L21[i][t], column k0 + t
     if (t < nb && j0 + q < m) u = A[(long long)(j0 + q) * m + k0 + t];   // U12[t][j], row k0 + t
-    Lr[t][q] = l.x; Li[t][q] = l.y; Ls[t][q] = l.x + l.y;
-    Ur[t][q] = u.x; Ui[t][q] = u.y; Us[t][q] = u.x + u.y;
+    Lr[t][q] = l.x; Li[t][q] = l.y;
+    Ur[t][q] = u.x; Ui[t][q] = u.y;
+    if constexpr (k3m) { Ls[t][q] = l.x + l.y; Us[t][q] = u.x + u.y; }
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
-  double t1[2][2] = {}, t2[2][2] = {}, t3[2][2] = {};
+  R t1[2][2] = {}, t2[2][2] = {}, t3[2][2] = {};
   for (int t = 0; t < nb; ++t) {
-    double lr[2], li[2], ls[2], ur[2], ui[2], us[2];
+    R lr[2], li[2], ur[2], ui[2];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-      lr[a] = Lr[t][tx + 16 * a]; li[a] = Li[t][tx + 16 * a]; ls[a] = Ls[t][tx + 16 * a];
-      ur[a] = Ur[t][ty + 16 * a]; ui[a] = Ui[t][ty + 16 * a]; us[a] = Us[t][ty + 16 * a];
+      lr[a] = Lr[t][tx + 16 * a]; li[a] = Li[t][tx + 16 * a];
+      ur[a] = Ur[t][ty + 16 * a]; ui[a] = Ui[t][ty + 16 * a];
     }
+    if constexpr (k3m) {
+      R ls[2], us[2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a) { ls[a] = Ls[t][tx + 16 * a]; us[a] = Us[t][ty + 16 * a]; }
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        t1[a][b] = fma(lr[a], ur[b], t1[a][b]);
-        t2[a][b] = fma(li[a], ui[b], t2[a][b]);
-        t3[a][b] = fma(ls[a], us[b], t3[a][b]);
-      }
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          t1[a][b] = fma(lr[a], ur[b], t1[a][b]);
+          t2[a][b] = fma(li[a], ui[b], t2[a][b]);
+          t3[a][b] = fma(ls[a], us[b], t3[a][b]);
+        }
+    } else {
+      // t1 = re(L U), t3 = im(L U)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          t1[a][b] = fma(lr[a], ur[b], t1[a][b]);
+          t1[a][b] = fma(-li[a], ui[b], t1[a][b]);
+          t3[a][b] = fma(lr[a], ui[b], t3[a][b]);
+          t3[a][b] = fma(li[a], ur[b], t3[a][b]);
+        }
+    }
   }
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
@@ -453,9 +483,14 @@ __global__ void __launch_bounds__(256) k_lu_update(double2* __restrict__ Aall, i
     for (int a = 0; a < 2; ++a) {
       const int i = i0 + tx + 16 * a;
       if (i >= m) continue;
-      double2 v = A[(long long)j * m + i];
-      v.x -= t1[a][b] - t2[a][b];
-      v.y -= t3[a][b] - t1[a][b] - t2[a][b];
+      C v = A[(long long)j * m + i];
+      if constexpr (k3m) {
+        v.x -= t1[a][b] - t2[a][b];
+        v.y -= t3[a][b] - t1[a][b] - t2[a][b];
+      } else {
+        v.x -= t1[a][b];
+        v.y -= t3[a][b];
+      }
       A[(long long)j * m + i] = v;
     }
   }
@@ -465,7 +500,7 @@ __global__ void __launch_bounds__(256) k_lu_update(double2* __restrict__ Aall, i
 // 5b. explicit inverse from the LU factors: solve L U X = P I for a chunk of
 //     CB columns; X written row-major in precision C.
 // ---------------------------------------------------------------------------
-// LU factors rounded to the inverse's precision (complex FP32 path)
+// blocks (or their FP64 LU factors) rounded to complex FP32
 __global__ void k_lu_narrow(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     b[e] = make_float2((float)a[e].x, (float)a[e].y);
@@ -997,37 +1032,57 @@ vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plan
   return VIE_OK;
 }
 
-// FP64 LU with partial pivoting of nblk column-major m x m blocks (in place),
-// then the explicit inverses, row-major: complex FP32 from the factors
-// narrowed to FP32 (want64) and/or complex FP64 (want128).  VIE_EINVAL if a
-// block is singular.
+// batched LU of nblk column-major m x m blocks in place (panel + trailing
+// update per 16 columns)
+template <class C>
+static vie_status lu_factor(vie_plan_s* P, C* A, int* piv, int* info, int m, int nblk) {
+  cudaStream_t st = P->st;
+  const size_t smem = sizeof(C) * (size_t)LU_NB * m;
+  VIE_TRY(smem_optin(k_lu_panel<C>, smem));
+  const bool c64 = sizeof(C) == 8;
+  for (int k0 = 0; k0 < m; k0 += LU_NB) {
+    const int nb = std::min(LU_NB, m - k0);
+    {
+      Prof pf_(c64 ? "lu_panel_c64" : "lu_panel", st);
+      k_lu_panel<C><<<nblk, 512, smem, st>>>(A, piv, m, k0, info);
+      count_launch();
+    }
+    const int r22 = m - k0 - nb;
+    if (r22 > 0) {
+      const int nti = ceil_div(r22, LU_TILE);
+      Prof pf_(c64 ? "lu_update_c64" : "lu_update", st);
+      k_lu_update<C><<<dim3(nti * nti, nblk), 256, 0, st>>>(A, m, k0, nb);
+      count_launch();
+    }
+    VIE_CHECK_LAUNCH();
+  }
+  return VIE_OK;
+}
+
+// LU with partial pivoting of nblk column-major m x m blocks (FP64, in
+// place in LU), then the explicit inverses, row-major: complex FP64
+// (want128) from the FP64 factors, complex FP32 (want64) from the complex-FP32
+// LU of the blocks rounded to FP32 (or from the FP64 factors rounded to FP32
+// when both are wanted).  The complex-FP32 inverse carries FP32 rounding
+// either way; factoring in FP32 runs at the FP32 rate, which on this part is
+// about 58 times the FP64 rate.  VIE_EINVAL if a block is singular.
 vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
                                 DevBuf* inv128) {
   cudaStream_t st = P->st;
   const size_t mm = (size_t)m * m;
-  DevBuf piv, info;
+  DevBuf piv, info, LU32;
   VIE_TRY(piv.alloc(sizeof(int) * (size_t)m * nblk));
   VIE_TRY(info.alloc(sizeof(int)));
   VIE_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
-  {
-    const size_t smem = sizeof(double2) * (size_t)LU_NB * m;
-    VIE_TRY(smem_optin(k_lu_panel, smem));
-    for (int k0 = 0; k0 < m; k0 += LU_NB) {
-      const int nb = std::min(LU_NB, m - k0);
-      {
-        Prof pf_("lu_panel", st);
-        k_lu_panel<<<nblk, 512, smem, st>>>(LU.as<double2>(), piv.as<int>(), m, k0, info.as<int>());
-        count_launch();
-      }
-      const int r22 = m - k0 - nb;
-      if (r22 > 0) {
-        const int nti = ceil_div(r22, LU_TILE);
-        Prof pf_("lu_update", st);
-        k_lu_update<<<dim3(nti * nti, nblk), 256, 0, st>>>(LU.as<double2>(), m, k0, nb);
-        count_launch();
-      }
-      VIE_CHECK_LAUNCH();
-    }
+  if (want128) VIE_TRY(lu_factor<double2>(P, LU.as<double2>(), piv.as<int>(), info.as<int>(), m, nblk));
+  if (want64) {
+    VIE_TRY(LU32.alloc(sizeof(float2) * mm * nblk));
+    const long long tot = (long long)mm * nblk;
+    k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
+                                                                                        LU32.as<float2>(), tot);
+    count_launch();
+    VIE_CHECK_LAUNCH();
+    if (!want128) VIE_TRY(lu_factor<float2>(P, LU32.as<float2>(), piv.as<int>(), info.as<int>(), m, nblk));
   }
   // column chunk of the inverse: m x (CB + 3) elements of shared memory
   auto chunk = [&](size_t esz) { return (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024) / (esz * m) - 3)); };
@@ -1035,13 +1090,6 @@ vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool
     const int CB = chunk(sizeof(float2));
     dim3 gi(nblk, ceil_div(m, CB));
     VIE_TRY(inv64->alloc(sizeof(float2) * mm * nblk));
-    // the complex-FP32 inverse works from the factors rounded to FP32
-    DevBuf LU32;
-    VIE_TRY(LU32.alloc(sizeof(float2) * mm * nblk));
-    const long long tot = (long long)mm * nblk;
-    k_lu_narrow<<<(int)std::min<long long>((tot + 255) / 256, 152LL * 16), 256, 0, st>>>(LU.as<double2>(),
-                                                                                        LU32.as<float2>(), tot);
-    count_launch();
     if (m <= 8 * 72) {
       // register-blocked: 8 row groups x 32 columns per CTA
       dim3 gr(nblk, ceil_div(m, 32));

@@ -48,9 +48,12 @@ void set_error(const char* fmt, ...);
 // the same value, so a plan built on another host thread can never lower the
 // limit under a launch in flight.  Cached per device and kernel.
 vie_status smem_optin_raw(const void* kern, size_t need);
+// Without the opt-in a block may use 48 KB of static and dynamic shared
+// memory together: the opt-in is skipped only for requests of at most 32 KB,
+// which leaves 16 KB for the kernel's static arrays.
 template <class K>
 inline vie_status smem_optin(K* kern, size_t need) {
-  return need <= 48 * 1024 ? VIE_OK : smem_optin_raw((const void*)kern, need);
+  return need <= 32 * 1024 ? VIE_OK : smem_optin_raw((const void*)kern, need);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,9 +6,16 @@ against the largest entry, and in norm); the FP64 preconditioner apply to
 1e-11 (LU + explicit inverse vs. LU solves, condition numbers of D_f ~ 1e2);
 complex-FP32 paths in norm and element-wise to the single-precision rounding
 of their arithmetic: 1e-6 for the matvec (unit roundoff 6e-8 times the ~15
-rounding steps of an FFT chain and the product) and 2e-6 for the
-preconditioner (the FP32 block inverse adds kappa(D_f) ~ 10 times that);
-solutions to 1e-6 relative error.
+rounding steps of an FFT chain and the product) and, for the preconditioner,
+whose blocks are factored and inverted in complex FP32, 2e-6 where every
+block is well conditioned (kappa(D_f) up to ~600: the measured error is
+2e-7 to 7e-7), and bounds that follow the worst block elsewhere: the
+elimination's FP32 rounding reaches the small pivots of a near-singular
+block with relative error ~ u32 kappa.  The 24x8 box of m = 576
+(kappa ~ 530, m three times larger) measures 5.3e-6 and takes 1.5e-5; the
+16x8-voxel Si core in air has one x-frequency block with kappa ~ 1e5
+(oracle blocks, numpy cond), measures 4.2e-5 and takes 1e-4.  Solutions to
+1e-6 relative error.
 """
 import dataclasses
 import math
@@ -26,6 +33,10 @@ from paper_1903_07884_gb300.solver import Plan, make_opts, to_device
 pytestmark = pytest.mark.gpu
 
 K0 = 2 * math.pi / 1.55
+
+# complex-FP32 preconditioner bounds of the cases with an ill-conditioned
+# block (module docstring); 2e-6 for the others
+C64_PRECOND_BOUND = {"wide_box_m576": 1.5e-5, "si_core_16x8": 1e-4}
 
 
 def _oracle_matvec(nx, ny, nz, h, k0, eps_bg, eps, x):
@@ -186,15 +197,17 @@ def test_precond_mixed_matches_oracle(name):
     plan.build()
     z = plan.precond(to_device(r), vie.VIE_MIXED).cpu().numpy()
     plan.close()
-    assert relerr(z, ref) <= 2e-6
-    assert maxerr(z, ref) <= 2e-6
+    bound = C64_PRECOND_BOUND.get(name, 2e-6)
+    assert relerr(z, ref) <= bound
+    assert maxerr(z, ref) <= bound
 
 
 def test_precond_mixed_tensor_core_block_product():
     """The discarded-frequency product with the representative block (Sec. 4.2)
     runs on the tensor cores in the mixed path (3xTF32 split, FP32-level
     accuracy): the 16x8 cross-section gives m = 384, and the discarded
-    frequencies fill 128-frequency tiles with a ragged last one."""
+    frequencies fill 128-frequency tiles with a ragged last one.  The bound is
+    that of the 16x8 Si core's near-singular block (module docstring)."""
     cuda_or_fail()
     p = inputs.straight_guide(320, 16, 8, 0.025, 1.55)
     tau = 1e-3
@@ -214,8 +227,8 @@ def test_precond_mixed_tensor_core_block_product():
     vie.vie_profile_enable(0)
     plan.close()
     assert table.get("rep_gemm_tc", (0, 0.0))[0] == 1, table
-    assert relerr(z, ref) <= 2e-6
-    assert maxerr(z, ref) <= 2e-5
+    assert relerr(z, ref) <= C64_PRECOND_BOUND["si_core_16x8"]
+    assert maxerr(z, ref) <= C64_PRECOND_BOUND["si_core_16x8"]
 
 
 @pytest.mark.parametrize("nx", [256, 512, 1024])
@@ -243,7 +256,7 @@ def test_precond_mixed_power_of_two_lines(nx):
     plan.close()
     assert table.get("fft_warp_c64", (0, 0.0))[0] == 2, table
     assert relerr(z, ref) <= 2e-6
-    assert maxerr(z, ref) <= 2e-5
+    assert maxerr(z, ref) <= 2e-6
 
 
 @pytest.mark.parametrize("precision,tol,bound", [(vie.VIE_FP64, 1e-11, 1e-7), (vie.VIE_MIXED, 1e-10, 1e-6)])
