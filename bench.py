@@ -859,6 +859,9 @@ def run_study(args):
              (mode, mean, real part of the mean) against the grating length
              (number of periods, width step 50 nm) and against the fill D/N as
              the corrugation depth grows (100 periods);
+    bragg_bench_shape - the same two sweeps on the benchmark grating's shape
+             (24x8 voxels, core 16/12, period 32, two x-boxes; 64 periods for
+             the depth sweep);
     length - Sec. 3 and 4: iterations of unpreconditioned GMRES against the
              length of a Si wire in air, beside the 1-level preconditioner;
     disk   - Sec. 5.3.1: disk resonators of radius 1-5 um beside a bus, with
@@ -905,6 +908,27 @@ def run_study(args):
             for v in (1, 2, 3):
                 it, rr = iters(p, homog=v)
                 rows.append({"sweep": "depth", "n_per": 100, "dW_nm": 25 * dw, "D_over_N": fill,
+                             "variant": names[v], "iters": it, "relres": rr})
+    elif args.study == "bragg_bench_shape":
+        # the benchmark grating's shape: 24x8 cross-section, core 16 voxels
+        # (400 nm) wide with 12-voxel narrow sections, period 32 (800 nm),
+        # h = 25 nm, lambda = 1.55 um, Si in SiO2, two x-boxes
+        wide, period = 16, 32
+        for nper in (8, 16, 32, 64, 128):
+            p = inputs.bragg_grating(nper * period, 24, 8, 0.025, 1.55, wide=wide, narrow=wide - 4, period=period,
+                                     name=f"bragg24_nper{nper}")
+            for v in (1, 2, 3):
+                it, rr = iters(p, homog=v)
+                rows.append({"sweep": "length", "n_per": nper, "dW_nm": 100, "variant": names[v], "iters": it,
+                             "relres": rr})
+        for dw in (0, 2, 4, 6, 8, 10):
+            p = inputs.bragg_grating(64 * period, 24, 8, 0.025, 1.55, wide=wide, narrow=wide - dw, period=period,
+                                     name=f"bragg24_dw{dw}")
+            x = np.arange(p.nx)
+            fill = float(np.mean(np.where((x % period) < period // 2, wide, wide - dw)) / wide)
+            for v in (1, 2, 3):
+                it, rr = iters(p, homog=v)
+                rows.append({"sweep": "depth", "n_per": 64, "dW_nm": 25 * dw, "D_over_N": fill,
                              "variant": names[v], "iters": it, "relres": rr})
     elif args.study == "disk":
         # Sec. 5.3.1, Table disk: 20 nm voxels, 220 nm slab, 400 nm bus, 200 nm
@@ -1015,7 +1039,7 @@ def main():
     ap.add_argument("--fp64-serial-n", type=int, default=16, help="requests of the serial FP64 serving leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
-    ap.add_argument("--study", choices=["bragg", "length", "disk"], default=None,
+    ap.add_argument("--study", choices=["bragg", "bragg_bench_shape", "length", "disk"], default=None,
                     help="qualitative iteration studies (prints one JSON line; not a bench line)")
     ap.add_argument("--precond2-case", action="store_true",
                     help="time the blocked 2-level preconditioner apply of a 3 um disk (prints no bench line)")

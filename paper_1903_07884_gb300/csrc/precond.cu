@@ -594,16 +594,29 @@ __global__ void __launch_bounds__(256) k_block_inv(const C* __restrict__ LUall, 
   }
 }
 
+// 8-byte global -> shared copy that does not hold the issuing thread
+// (cp.async; completion by commit groups)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the most recent group of this thread complete
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Register-blocked variant for m <= 8 RPG (complex FP32): 256 threads = 8
 // row groups (one per warp) x 32 right-hand-side columns; thread (g, c) keeps
 // rows [g RPG, (g + 1) RPG) of column c in registers.  Per step the owner of
 // row k publishes it through shared memory (one barrier), and every thread
 // updates its own rows with the staged factor column, so the update touches
 // shared memory once per multiply-add (the factor) instead of four times.
+// The factor columns stream through three shared buffers, copied two steps
+// ahead with cp.async, so no step waits on a global load.
 template <int RPG>
 __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__ LUall, const int* __restrict__ pivall,
                                                       float2* __restrict__ invall, int m) {
-  __shared__ float2 col[2][8 * RPG];
+  __shared__ __align__(16) float2 col[3][8 * RPG];
   __shared__ float2 rowk[2][32];
   __shared__ float2 dinv[8 * RPG];
   __shared__ int pv[8 * RPG];
@@ -613,6 +626,20 @@ __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__
   const int j0 = blockIdx.y * 32;
   const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
   const int r0 = g * RPG;
+  // L column k below the diagonal (rows k + 1 .. m - 1) into buffer k % 3
+  auto fetch_l = [&](int k) {
+    if (k < m - 1)
+      for (int i = k + 1 + tid; i < m; i += 256) cp_async8(&col[k % 3][i], LU + (long long)k * m + i);
+    cp_async_commit();
+  };
+  // U column k above the diagonal (rows 0 .. k - 1) into buffer (m - 1 - k) % 3
+  auto fetch_u = [&](int k) {
+    if (k > 0)
+      for (int i = tid; i < k; i += 256) cp_async8(&col[(m - 1 - k) % 3][i], LU + (long long)k * m + i);
+    cp_async_commit();
+  };
+  fetch_l(0);
+  fetch_l(1);
   for (int k = tid; k < m; k += 256) {
     const float2 u = LU[(long long)k * m + k];
     const float q = 1.f / (u.x * u.x + u.y * u.y);
@@ -630,21 +657,21 @@ __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__
   float2 y[RPG];
 #pragma unroll
   for (int q = 0; q < RPG; ++q) y[q] = make_float2((j0 + c < m && r0 + q == one) ? 1.f : 0.f, 0.f);
-  // forward substitution with unit lower L (column k of L staged one step ahead)
-  for (int i = 1 + tid; i < m; i += 256) col[0][i] = LU[i];
+  // forward substitution with unit lower L
   if (r0 <= 0 && 0 < r0 + RPG) rowk[0][c] = y[0];
+  cp_async_wait1();   // column 0
   __syncthreads();
   for (int k = 0; k < m - 1; ++k) {
     const int b = k & 1;
-    if (k + 1 < m - 1)
-      for (int i = k + 2 + tid; i < m; i += 256) col[b ^ 1][i] = LU[(long long)(k + 1) * m + i];
+    fetch_l(k + 2);
+    const float2* lk = col[k % 3];
     const float2 yk = rowk[b][c];
     if (r0 + RPG > k + 1) {   // warp-uniform: this row group still has rows below k
 #pragma unroll
       for (int q = 0; q < RPG; ++q) {
         const int i = r0 + q;
         if (i > k && i < m) {
-          const float2 l = col[b][i];
+          const float2 l = lk[i];
           y[q].x -= l.x * yk.x - l.y * yk.y;
           y[q].y -= l.x * yk.y + l.y * yk.x;
         }
@@ -656,20 +683,25 @@ __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__
       for (int q = 0; q < RPG; ++q)
         if (r0 + q == k + 1) rowk[b ^ 1][c] = y[q];
     }
+    cp_async_wait1();   // column k + 1
     __syncthreads();
   }
   // back substitution with U: row k of the result is y_k / U[k][k]
-  for (int i = tid; i < m - 1; i += 256) col[0][i] = LU[(long long)(m - 1) * m + i];
+  cp_async_wait0();
+  __syncthreads();     // every buffer free
+  fetch_u(m - 1);
+  fetch_u(m - 2);
   if (r0 <= m - 1 && m - 1 < r0 + RPG) {
 #pragma unroll
     for (int q = 0; q < RPG; ++q)
       if (r0 + q == m - 1) rowk[0][c] = y[q];
   }
+  cp_async_wait1();   // column m - 1
   __syncthreads();
   for (int k = m - 1; k >= 0; --k) {
     const int b = (m - 1 - k) & 1;
-    if (k > 0)
-      for (int i = tid; i < k - 1; i += 256) col[b ^ 1][i] = LU[(long long)(k - 1) * m + i];
+    fetch_u(k - 2);
+    const float2* uk = col[(m - 1 - k) % 3];
     const float2 yk = cmul(rowk[b][c], dinv[k]);
     if (g == 0 && j0 + c < m) inv[(long long)k * m + j0 + c] = yk;
     if (r0 < k) {
@@ -677,7 +709,7 @@ __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__
       for (int q = 0; q < RPG; ++q) {
         const int i = r0 + q;
         if (i < k) {
-          const float2 u = col[b][i];
+          const float2 u = uk[i];
           y[q].x -= u.x * yk.x - u.y * yk.y;
           y[q].y -= u.x * yk.y + u.y * yk.x;
         }
@@ -688,8 +720,10 @@ __global__ void __launch_bounds__(256) k_block_inv_rb(const float2* __restrict__
       for (int q = 0; q < RPG; ++q)
         if (r0 + q == k - 1) rowk[b ^ 1][c] = y[q];
     }
+    cp_async_wait1();   // column k - 1
     __syncthreads();
   }
+  cp_async_wait0();
 }
 
 // ---------------------------------------------------------------------------
