@@ -269,7 +269,8 @@ vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double
  * the generic kernels) and its x pass (compile-time radix-16 kernel or the generic Stockham
  * kernel with one of three radix orders, per precision), timed at plan
  * creation, and each box's kept-block product (1, 2, 4 or 8 CTAs per
- * block), timed at preconditioner build.  Choices are cached per process and
+ * block) and tensor-core representative-block product (N tile of 64 or 32
+ * columns), timed at preconditioner build.  Choices are cached per process and
  * shape; VIE_AUTOTUNE=0 in the environment keeps the default rules, and a
  * file named by VIE_TUNE_FILE keeps the choices across processes (read at
  * the first lookup, appended to by each new choice).  The
@@ -283,8 +284,9 @@ const char* vie_plan_tuning(vie_plan_t plan);
  * complex FP32, L = 4096 or 8192); "yz_passes_c64" with 16, 8 or 4 x-columns
  * per CTA of the register yz passes; "yz_generic_c64" with 1, 2, 4, 8 or 16
  * x-columns per CTA of the generic yz passes (as shared memory allows);
- * "block_gemv" with 1, 2, 4 or 8 CTAs per kept block (set on the
- * built preconditioner; a rebuild tunes again).  VIE_EINVAL for a variant that
+ * "block_gemv" with 1, 2, 4 or 8 CTAs per kept block, "rep_gemm_tc" with
+ * an N tile of 64 or 32 columns for the complex-FP32 representative-block
+ * product (both set on the built preconditioner; a rebuild tunes again).  VIE_EINVAL for a variant that
  * does not exist for the plan's shape. */
 vie_status vie_plan_set_tuning(vie_plan_t plan, const char* kernel, int choice);
 

@@ -69,6 +69,7 @@ struct BoxPrec {
   DevBuf zhat64, zhat128;
   DevBuf tmp64, tmp128;      // transform scratch (Bluestein and/or long-line split)
   DevBuf bpack, apack;       // tensor-core operands of the representative-block product (packed tf32 hi/lo)
+  int tc_n = 64;             // N tile of that product (64 or 32; set by the autotuner)
   int gemv_split[2] = {0, 0};  // kept-block product: CTAs per block, complex FP32 / FP64 (0: the default
                                // rule; set by the autotuner)
   const FftLen* fx = nullptr;
@@ -191,6 +192,7 @@ template <class C>
 vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st);
 void precond_free(vie_plan_s* P);
 vie_status precond_add_fp64(vie_plan_s* P);
+vie_status precond_set_rep_tile(vie_plan_s* P, int tn);
 vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plane);
 vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
                                 DevBuf* inv128);

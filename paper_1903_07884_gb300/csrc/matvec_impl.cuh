@@ -672,6 +672,26 @@ __global__ void __launch_bounds__(128) k_mv_yz_inv_r(const float2* __restrict__ 
   const int a = blockIdx.y, x0 = blockIdx.x * YZ_XG;
   const int xg = min(YZ_XG, d.nx - x0);
   const float2* Ta = T + (long long)a * PZ * PY * d.nx;
+  const long long plane = (long long)d.ny * d.nx;
+  const long long off_a = (long long)a * d.nz * plane;
+  // the epilogue's x and M of this thread's first output row, loaded before
+  // the transforms so that their latency hides behind them
+  float2 xp[PY / 2], mp[PY / 2];
+  {
+    const int ln = threadIdx.x;
+    const int xl = ln % YZ_XG, z = ln / YZ_XG;
+    const bool own = ln < d.nz * YZ_XG && xl < xg;
+#pragma unroll
+    for (int yy = 0; yy < PY / 2; ++yy) {
+      xp[yy] = make_float2(0.f, 0.f);
+      mp[yy] = make_float2(0.f, 0.f);
+      if (own && yy < d.ny) {
+        const long long vox = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
+        xp[yy] = x[off_a + vox];
+        mp[yy] = Mv[vox];
+      }
+    }
+  }
   // inverse z transforms of the columns (xl, ky); keep the rows z < nz
   for (int ln = threadIdx.x; ln < YZ_XG * PY; ln += blockDim.x) {
     const int xl = ln % YZ_XG, ky = ln / YZ_XG;
@@ -686,8 +706,6 @@ __global__ void __launch_bounds__(128) k_mv_yz_inv_r(const float2* __restrict__ 
   }
   __syncthreads();
   // inverse y transforms of the rows z < nz, crop to ny, y = x - M (x + G x)
-  const long long plane = (long long)d.ny * d.nx;
-  const long long off_a = (long long)a * d.nz * plane;
   for (int ln = threadIdx.x; ln < d.nz * YZ_XG; ln += blockDim.x) {
     const int xl = ln % YZ_XG, z = ln / YZ_XG;
     float2 v[PY];
@@ -695,12 +713,13 @@ __global__ void __launch_bounds__(128) k_mv_yz_inv_r(const float2* __restrict__ 
     for (int ky = 0; ky < PY; ++ky) v[ky] = S[(z * YZ_XG + xl) * PITCH + ky];
     dft_p2<PY, +1>(v);
     if (xl < xg) {
+      const bool first = ln == (int)threadIdx.x;
 #pragma unroll
       for (int yy = 0; yy < PY / 2; ++yy) {
         if (yy < d.ny) {
           const long long vox = (long long)z * plane + (long long)yy * d.nx + x0 + xl;
-          const float2 xv = x[off_a + vox];
-          const float2 mv = Mv[vox];
+          const float2 xv = first ? xp[yy] : x[off_a + vox];
+          const float2 mv = first ? mp[yy] : Mv[vox];
           y[off_a + vox] = csub(xv, cmul(mv, cadd(xv, v[yy])));
         }
       }

@@ -869,11 +869,13 @@ __global__ void __launch_bounds__(256) k_rep_gemm(const C* __restrict__ Drep, co
 // build, A by a gather kernel per apply.  The GEMM is a TC_STAGES-deep ring:
 // one thread issues the bulk copies, one issues the MMAs, and the commit of a
 // chunk's MMAs frees its stage.
-constexpr int TC_M = 128, TC_N = 64, TC_KC = 32, TC_STAGES = 4;
+// The N tile (TN = 64 or 32 columns of C, i.e. 32 or 16 rows of D) is chosen
+// per shape by the autotuner: the smaller tile runs twice the CTAs.
+constexpr int TC_M = 128, TC_KC = 32, TC_STAGES = 4;
 constexpr int TC_ACHUNK = 2 * TC_M * TC_KC;   // floats per packed A chunk (hi + lo)
-constexpr int TC_BCHUNK = 2 * TC_N * TC_KC;   // floats per packed B chunk (hi + lo)
-constexpr int TC_STAGE_BYTES = (TC_ACHUNK + TC_BCHUNK) * 4;
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES;
+__host__ __device__ constexpr int tc_bchunk(int tn) { return 2 * tn * TC_KC; }   // floats per packed B chunk
+__host__ __device__ constexpr int tc_stage_bytes(int tn) { return (TC_ACHUNK + tc_bchunk(tn)) * 4; }
+constexpr size_t tc_smem(int tn) { return (size_t)TC_STAGES * tc_stage_bytes(tn); }
 
 // (row, k) of slot q of a K-major core-matrix chunk with TC_KC columns
 __device__ __forceinline__ void tc_slot(int q, int& row, int& k) {
@@ -882,23 +884,25 @@ __device__ __forceinline__ void tc_slot(int q, int& row, int& k) {
 }
 
 // B operand of one representative block, packed [N tile][chunk][hi | lo]
+template <int TN>
 __global__ void k_bpack(const float2* __restrict__ D, float* __restrict__ Bp, int m) {
+  constexpr int TC_BCHUNK = tc_bchunk(TN);
   const int nchunks = 2 * m / TC_KC;
-  const long long total = (long long)(2 * m / TC_N) * nchunks * (TC_N * TC_KC);
+  const long long total = (long long)(2 * m / TN) * nchunks * (TN * TC_KC);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % (TC_N * TC_KC));
-    const int ct = (int)(e / (TC_N * TC_KC));
+    const int q = (int)(e % (TN * TC_KC));
+    const int ct = (int)(e / (TN * TC_KC));
     const int nt = ct / nchunks, c = ct - nt * nchunks;
     int row, k;
     tc_slot(q, row, k);
-    const int nrow = nt * TC_N + row, kg = c * TC_KC + k;
+    const int nrow = nt * TN + row, kg = c * TC_KC + k;
     const float2 d = D[(long long)(nrow >> 1) * m + (kg >> 1)];
     const int co = nrow & 1, ci = kg & 1;
     const float v = co == 0 ? (ci == 0 ? d.x : -d.y) : (ci == 0 ? d.y : d.x);
     float hi, lo;
     umma::split_tf32(v, hi, lo);
     Bp[(long long)ct * TC_BCHUNK + q] = hi;
-    Bp[(long long)ct * TC_BCHUNK + TC_N * TC_KC + q] = lo;
+    Bp[(long long)ct * TC_BCHUNK + TN * TC_KC + q] = lo;
   }
 }
 
@@ -925,9 +929,12 @@ __global__ void k_apack(const float2* __restrict__ R, const int* __restrict__ di
   }
 }
 
+template <int TC_N>
 __global__ void __launch_bounds__(128) k_rep_gemm_tc(const float* __restrict__ Ap, const float* __restrict__ Bp,
                                                      const int* __restrict__ disc, int ndisc,
                                                      float2* __restrict__ Z, int m, int n, int* __restrict__ err) {
+  constexpr int TC_BCHUNK = tc_bchunk(TC_N);
+  constexpr int TC_STAGE_BYTES = tc_stage_bytes(TC_N);
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
   __shared__ uint32_t tslot;
@@ -1018,6 +1025,85 @@ __global__ void __launch_bounds__(128) k_rep_gemm_tc(const float* __restrict__ A
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 2) umma::tmem_dealloc(tmem, TC_N);
+}
+
+// the representative block's B operand packed for N tile tn (64 or 32)
+static vie_status rep_pack(vie_plan_s* P, BoxPrec& B, int tn) {
+  const int m = B.m;
+  const long long nch = 2LL * m / TC_KC;
+  VIE_TRY(B.bpack.alloc(sizeof(float) * (size_t)(2 * m / tn) * nch * tc_bchunk(tn)));
+  const float2* rep = B.inv64.as<float2>() + (size_t)B.rep * m * m;
+  Prof pf_("bpack", P->st);
+  if (tn == 64) k_bpack<64><<<152 * 4, 256, 0, P->st>>>(rep, B.bpack.as<float>(), m);
+  else k_bpack<32><<<152 * 4, 256, 0, P->st>>>(rep, B.bpack.as<float>(), m);
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  B.tc_n = tn;
+  return VIE_OK;
+}
+
+// the discarded frequencies' product on the tensor cores with the packed N tile
+static vie_status launch_rep_tc(vie_plan_s* P, BoxPrec& B, float2* zh, cudaStream_t st) {
+  const int m = B.m;
+  Prof pf_("rep_gemm_tc", st);
+  dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / B.tc_n);
+  if (B.tc_n == 64) {
+    VIE_TRY(smem_optin(k_rep_gemm_tc<64>, tc_smem(64)));
+    k_rep_gemm_tc<64><<<grid, 128, tc_smem(64), st>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(),
+                                                      B.ndisc, zh, m, B.n, P->dev_err.as<int>());
+  } else {
+    VIE_TRY(smem_optin(k_rep_gemm_tc<32>, tc_smem(32)));
+    k_rep_gemm_tc<32><<<grid, 128, tc_smem(32), st>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(),
+                                                      B.ndisc, zh, m, B.n, P->dev_err.as<int>());
+  }
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
+// autotuner: N tile of the tensor-core product (64 or 32; the MMAs of every
+// output element run the same K chunks in the same order either way), timed
+// on the box's own operands, cached per shape
+static vie_status tune_rep_tc(vie_plan_s* P, BoxPrec& B) {
+  if (!autotune_enabled() || (2 * B.m) % 64 != 0) return VIE_OK;
+  const TuneKey key{4, 0, B.m, B.ndisc, B.n};
+  int choice;
+  std::string rep;
+  if (!tune_cache_get(key, &choice, &rep)) {
+    VIE_CUDA(cudaMemsetAsync(B.apack.p, 0, B.apack.bytes, P->st));
+    char buf[160];
+    snprintf(buf, sizeof(buf), "rep_gemm_tc m=%d discarded=%d n=%d:", B.m, B.ndisc, B.n);
+    rep = buf;
+    int best = 0;
+    float tbest = 0;
+    for (int tn : {64, 32}) {
+      VIE_TRY(rep_pack(P, B, tn));
+      float ms = 0;
+      VIE_TRY(time_ms(P->st, 3, [&] { return launch_rep_tc(P, B, B.zhat64.as<float2>(), P->st); }, &ms));
+      snprintf(buf, sizeof(buf), " N tile %d %.4f ms;", tn, ms);
+      rep += buf;
+      if (best == 0 || ms < tbest) { best = tn; tbest = ms; }
+    }
+    snprintf(buf, sizeof(buf), " chosen %d\n", best);
+    rep += buf;
+    choice = best;
+    tune_cache_put(key, choice, rep);
+  }
+  if (B.tc_n != choice) VIE_TRY(rep_pack(P, B, choice));
+  P->tuning += rep;
+  return VIE_OK;
+}
+
+// force the N tile of every box's tensor-core product (test hook)
+vie_status precond_set_rep_tile(vie_plan_s* P, int tn) {
+  for (auto& Bp : P->bp) {
+    BoxPrec& B = *Bp;
+    if (!B.bpack.p) continue;
+    if ((2 * B.m) % tn != 0) { set_error("vie_plan_set_tuning: 2m is not a multiple of the N tile"); return VIE_EINVAL; }
+    VIE_TRY(rep_pack(P, B, tn));
+  }
+  VIE_CUDA(cudaStreamSynchronize(P->st));
+  return VIE_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1283,14 +1369,10 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
     VIE_TRY(B.rhat64.alloc(sizeof(float2) * (size_t)n * m));
     VIE_TRY(B.zhat64.alloc(sizeof(float2) * (size_t)n * m));
     // tensor-core operands of the representative-block product (tf32 hi/lo split)
-    if ((2 * m) % TC_N == 0 && B.ndisc > 0) {
+    if ((2 * m) % 32 == 0 && B.ndisc > 0) {
       const long long nch = 2LL * m / TC_KC;
-      VIE_TRY(B.bpack.alloc(sizeof(float) * (size_t)(2 * m / TC_N) * nch * TC_BCHUNK));
       VIE_TRY(B.apack.alloc(sizeof(float) * (size_t)ceil_div(B.ndisc, TC_M) * nch * TC_ACHUNK));
-      Prof pf_("bpack", st);
-      k_bpack<<<152 * 4, 256, 0, st>>>(B.inv64.as<float2>() + (size_t)B.rep * m * m, B.bpack.as<float>(), m);
-      count_launch();
-      VIE_CHECK_LAUNCH();
+      VIE_TRY(rep_pack(P, B, (2 * m) % 64 == 0 ? 64 : 32));
     }
     const size_t ts = fft_scratch_elems<float2>(*B.fx, m);
     if (ts) VIE_TRY(B.tmp64.alloc(sizeof(float2) * ts));
@@ -1303,6 +1385,7 @@ static vie_status build_box(vie_plan_s* P, BoxPrec& B, bool want64, bool want128
   }
   if (want64) VIE_TRY(tune_gemv<float2>(P, B, 0));
   if (want128) VIE_TRY(tune_gemv<double2>(P, B, 1));
+  if (want64 && B.bpack.p) VIE_TRY(tune_rep_tc(P, B));
   return VIE_OK;
 }
 
@@ -1417,15 +1500,7 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st) {
         count_launch();
         VIE_CHECK_LAUNCH();
       }
-      {
-        Prof pf_("rep_gemm_tc", s2);
-        VIE_TRY(smem_optin(k_rep_gemm_tc, TC_SMEM));
-        dim3 grid(ceil_div(B.ndisc, TC_M), (2 * m) / TC_N);
-        k_rep_gemm_tc<<<grid, 128, TC_SMEM, s2>>>(B.apack.as<float>(), B.bpack.as<float>(), B.disc.as<int>(), B.ndisc,
-                                                  (float2*)zh, m, n, P->dev_err.as<int>());
-        count_launch();
-        VIE_CHECK_LAUNCH();
-      }
+      VIE_TRY(launch_rep_tc(P, B, (float2*)zh, s2));
     }
     if (B.nhalf > 0) VIE_TRY(launch_block_gemv<C>(B, inv, rh, zh, B.gemv_split[sizeof(C) == 16], st));
     if (tc) {

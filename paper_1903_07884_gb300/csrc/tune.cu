@@ -301,6 +301,9 @@ extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int 
       return VIE_EINVAL;
     }
     for (auto& B : P->bp) B->gemv_split[P->opts.precision == VIE_FP64] = choice;
+  } else if (k == "rep_gemm_tc") {
+    if (choice != 64 && choice != 32) { set_error("vie_plan_set_tuning: the N tile must be 64 or 32"); return VIE_EINVAL; }
+    VIE_TRY(precond_set_rep_tile(P, choice));
   } else {
     set_error("vie_plan_set_tuning: unknown kernel '%s'", kernel);
     return VIE_EINVAL;

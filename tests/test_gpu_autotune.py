@@ -151,6 +151,20 @@ def test_every_yz_and_gemv_choice_matches_oracle():
         outs.append(z)
     for z in outs[1:]:   # the split does not change a single bit
         np.testing.assert_array_equal(z, outs[0])
+    # the tensor-core product of the discarded frequencies: both N tiles run
+    # the same K chunks in the same order for every output element
+    rep = vie.vie_plan_tuning(plan.handle)
+    lines = _xpass_lines(rep, "rep_gemm_tc")
+    assert len(lines) == 1, rep
+    assert [int(t) for t in re.findall(r"N tile (\d+) ", lines[0])] == [64, 32], lines[0]
+    tiles = []
+    for tn in (64, 32):
+        assert vie.vie_plan_set_tuning(plan.handle, "rep_gemm_tc", tn) == vie.VIE_OK
+        z = plan.precond(xd, vie.VIE_MIXED).cpu().numpy()
+        assert relerr(z, zref) <= 1e-4 and maxerr(z, zref) <= 1e-4, tn
+        tiles.append(z)
+    np.testing.assert_array_equal(tiles[1], tiles[0])
+    assert vie.vie_plan_set_tuning(plan.handle, "rep_gemm_tc", 48) == vie.VIE_EINVAL
     plan.close()
 
 
