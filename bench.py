@@ -172,13 +172,15 @@ def algorithmic(kernel: str, p, plan_meta: dict):
     return None
 
 
-# DRAM bytes per launch from the ncu step capture of the same kernel versions
-# (the --set full capture of one GMRES step of the 1024x16x8 wire):
-# per basis column read for the Arnoldi kernels (120.4 MB at j = 36, 38
-# columns), per launch for the others.  Cleared whenever a kernel changes.
+# DRAM bytes (read + write) per launch from one ncu --set full capture of the
+# same kernel versions on the 1024x16x8 wire: per basis column read for the
+# Arnoldi reduction (325.7 MB at step j = 100, j + 2 = 102 columns), per
+# launch for the others.  Cleared whenever a kernel changes.
 TRAFFIC = {
     "long_straight_1024x16x8": {
+        "arnoldi_dot_c64": ("per_column", 325.70e6 / 102),
         "mv_x_c64": ("per_launch", 20.23e6),
+        "block_gemv_c64": ("per_launch", 132.30e6),
     }
 }
 
