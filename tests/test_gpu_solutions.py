@@ -20,7 +20,7 @@ import pytest
 from gpu_common import cuda_or_fail, maxerr, relerr
 from oracle import solve as osolve
 from paper_1903_07884_gb300 import inputs, vie
-from paper_1903_07884_gb300.solver import Plan
+from paper_1903_07884_gb300.solver import Plan, make_opts, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -126,3 +126,43 @@ def test_coupler_full_size_solution_matches_oracle_sample(precision):
     assert info["relres"] <= 1e-9
     assert relerr(ws, ref) <= 1e-6, info
     assert maxerr(ws, ref) <= 1e-6, info
+
+
+def test_coupler_wavelength_batch_matches_solo_solves_and_oracle_sample():
+    """Two wavelengths of the 2048x48x8 coupler sweep (1.50 and 1.55 um) in
+    one lockstep batch (vie_solve_batch): each result bitwise equal to the
+    same plan solved alone, and the 1.50 um result within 1e-6 of the
+    oracle's stored solution sample."""
+    torch = cuda_or_fail()
+    name = "coupler_2048x48x8_2boxes_lambda1.50"
+    meta = json.load(open(os.path.join(GOLDEN, "oracle_solutions.json")))[name]
+    d = np.load(os.path.join(GOLDEN, meta["file"]))
+    idx, ref = d["idx"], d["w"]
+    probs = [inputs.workload_coupler(wavelength=lam) for lam in (1.50, 1.55)]
+    alone = []
+    for p in probs:
+        plan = Plan.for_problem(p, tol=1e-9)
+        plan.set_permittivity(p.eps)
+        w, info = plan.solve(p.e_inc)
+        assert info["relres"] <= 1e-9
+        alone.append(w.cpu().numpy())
+        plan.close()
+    plans, es, ws = [], [], []
+    for p in probs:
+        pl = Plan(p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, make_opts(tol=1e-9, boxes=p.boxes or None, homog=p.homog))
+        pl.set_permittivity(p.eps)
+        e = to_device(p.e_inc)
+        es.append(e)
+        ws.append(torch.empty_like(e))
+        plans.append(pl)
+    torch.cuda.synchronize()
+    infos = vie.vie_solve_batch([pl.handle for pl in plans], [e.data_ptr() for e in es], [w.data_ptr() for w in ws])
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert infos[i].relres <= 1e-9
+        np.testing.assert_array_equal(ws[i].cpu().numpy(), alone[i])
+    wb = ws[0].cpu().numpy().ravel()[idx]
+    assert relerr(wb, ref) <= 1e-6
+    assert maxerr(wb, ref) <= 1e-6
+    for pl in plans:
+        pl.close()
