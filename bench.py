@@ -534,7 +534,7 @@ def run_gpu(args):
 
     if args.serving_n > 0:
         line["serving"] = run_serving(args.serving_n, args.inflight, args.budget_gb, args.tol, args.fp64_serial_s,
-                                      args.fp64_serial_n)
+                                      args.fp64_serial_n, args.mixed_serial_n)
 
     ref = oracle_solution(wname)
     if ref is not None:
@@ -572,12 +572,15 @@ def run_gpu(args):
     return 0
 
 
-def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_limit_s: float, fp64_n: int = 16):
+def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_limit_s: float, fp64_n: int = 16,
+                mixed_serial_n: int = 0):
     """Replay the first n_req requests of the seeded serving stream (Poisson
     arrivals, 50/s) against the continuous-batching server; every request is
     submitted at its arrival time with host buffers and its latency runs from
     arrival to completion.  The same requests are then solved one by one with
-    the plain FP64 GPU method (time-bounded by fp64_limit_s)."""
+    the plain FP64 GPU method (time-bounded by fp64_limit_s) and, if
+    mixed_serial_n > 0, the first mixed_serial_n of them one by one with the
+    same mixed method outside the server (what continuous batching gains)."""
     import numpy as np
 
     from paper_1903_07884_gb300 import inputs, vie
@@ -658,6 +661,25 @@ def run_serving(n_req: int, inflight: int, budget_gb: float, tol: float, fp64_li
         lat64.append(1000.0 * (time.perf_counter() - ts))
         if status.get(i) in (vie.VIE_OK, vie.VIE_ENOCONV):
             errs.append(float(np.linalg.norm(w_srv - w) / np.linalg.norm(w)))
+    if mixed_serial_n > 0:
+        latm, parts = [], []
+        for i, p in enumerate(probs[:mixed_serial_n]):
+            eps, e, _ = bufs[i]
+            w = np.empty(p.e_inc.shape, dtype=np.complex128)
+            opts = make_opts(precision=vie.VIE_MIXED, tol=tol, boxes=p.boxes or None, homog=p.homog)
+            ts = time.perf_counter()
+            plan = vie.vie_plan_create(p.nx, p.ny, p.nz, p.h, p.k0, p.eps_bg, opts, 0)
+            tc = time.perf_counter()
+            info = vie.vie_solve_host(plan, eps.ctypes.data, e.ctypes.data, w.ctypes.data, allow_noconv=True)
+            vie.vie_plan_destroy(plan)
+            latm.append(time.perf_counter() - ts)
+            parts.append((tc - ts, info.t_setup_ms / 1e3, info.t_solve_ms / 1e3))
+        out["mixed_serial"] = {"requests": len(latm), "solves_per_s": len(latm) / sum(latm),
+                               "seconds": {"plan_create": sum(a for a, _, _ in parts),
+                                           "precond_build": sum(b for _, b, _ in parts),
+                                           "solve_incl_build": sum(c for _, _, c in parts), "total": sum(latm)},
+                               "note": "the same mixed method, each request alone through vie_plan_create + "
+                                       "vie_solve_host, first requests of the same stream"}
     if lat64:
         out["fp64_serial"] = {"requests": len(lat64), "solves_per_s": len(lat64) / (sum(lat64) / 1000.0),
                               "p50_ms": float(np.percentile(lat64, 50)), "p99_ms": float(np.percentile(lat64, 99)),
@@ -1040,6 +1062,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=220.0)
     ap.add_argument("--fp64-serial-s", type=float, default=30.0, help="time bound of the serial FP64 serving leg")
     ap.add_argument("--fp64-serial-n", type=int, default=16, help="requests of the serial FP64 serving leg")
+    ap.add_argument("--mixed-serial-n", type=int, default=0,
+                    help="requests solved one by one with the mixed method outside the server (0 = skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     ap.add_argument("--study", choices=["bragg", "bragg_bench_shape", "length", "disk"], default=None,

@@ -266,8 +266,9 @@ vie_status vie_matvec_static(int nx, int ny, int nz, double h, double k0, double
 /* The autotuner's report for the plan: per tuned kernel the shape, each
  * candidate launch variant with its measured device time (ms) and the
  * choice -- the matvec's yz passes (x-columns per CTA of the register or of
- * the generic kernels) and its x pass (compile-time radix-16 kernel or the generic Stockham
- * kernel with one of three radix orders, per precision), timed at plan
+ * the generic kernels) and its x pass (compile-time radix-16 kernel, the
+ * generic Stockham kernel with one of three radix orders, or the kernel split
+ * over a cluster of CTAs, per precision), timed at plan
  * creation, and each box's kept-block product (1, 2, 4 or 8 CTAs per
  * block) and tensor-core representative-block product (N tile of 64 or 32
  * columns), timed at preconditioner build.  Choices are cached per process and
@@ -280,8 +281,10 @@ const char* vie_plan_tuning(vie_plan_t plan);
 /* Test hook: override one of the autotuner's choices for this plan.  kernel
  * "x_pass_c64" / "x_pass_c128" with choice -1 (default rule), 0 (three-pass
  * compile-time kernel, complex FP32, L = 2048 or 4096), 1..3 (generic
- * Stockham kernel with radix order 1..3) or 4 (four-pass compile-time kernel,
- * complex FP32, L = 4096 or 8192); "yz_passes_c64" with 16, 8 or 4 x-columns
+ * Stockham kernel with radix order 1..3), 4 (four-pass compile-time kernel,
+ * complex FP32, L = 4096 or 8192) or 5 (complex FP32: the x pass split over a
+ * cluster of 2 or 4 CTAs, for embeddings whose three lines do not fit one
+ * CTA's shared memory); "yz_passes_c64" with 16, 8 or 4 x-columns
  * per CTA of the register yz passes; "yz_generic_c64" with 1, 2, 4, 8 or 16
  * x-columns per CTA of the generic yz passes (as shared memory allows);
  * "block_gemv" with 1, 2, 4 or 8 CTAs per kept block, "rep_gemm_tc" with

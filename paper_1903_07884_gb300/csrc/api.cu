@@ -98,6 +98,23 @@ static bool boxes_valid(int nx, int ny, int nz, const std::vector<vie_box>& bs) 
 
 static int embed_len(int n) { return 2 * fft_next_smooth(n); }
 
+// x-embedding (any L >= 2 nx - 1 gives the same matvec): 2 smooth(nx), whose
+// three complex-FP32 lines one CTA transforms when they fit shared memory
+// (or L = 4096, 8192, the compile-time kernels); past that the x pass splits
+// the frequencies over a cluster of 2 CTAs (lines of L/2), then of 4 CTAs
+// with L = 4 smooth(ceil(nx / 2)) >= 2 nx (lines of L/4); beyond that the
+// unfused path through the full x-spectrum.
+int embed_x(int nx, int* q) {
+  const int L = embed_len(nx);
+  const int lq_max = (int)((200 * 1024) / (2 * 3 * sizeof(float2)));   // three lines, two copies
+  *q = 1;
+  if (L <= lq_max || L == 4096 || L == 8192) return L;
+  if (L / 2 <= lq_max) { *q = 2; return L; }
+  const int L4 = 4 * fft_next_smooth((nx + 1) / 2);
+  if (L4 / 4 <= lq_max) { *q = 4; return L4; }
+  return L;
+}
+
 std::atomic<int> g_prof_on{0};
 struct ProfRec { const char* name; cudaEvent_t e0, e1; };
 static std::mutex g_prof_mu;
@@ -261,7 +278,7 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   StreamScope scope(P->st);
   MvDims& d = P->d;
   d.nx = nx; d.ny = ny; d.nz = nz;
-  d.L = embed_len(nx); d.Py = embed_len(ny); d.Pz = embed_len(nz);
+  d.L = embed_x(nx, &P->xq); d.Py = embed_len(ny); d.Pz = embed_len(nz);
   d.Lh = d.L / 2 + 1; d.Pyh = d.Py / 2 + 1; d.Pzh = d.Pz / 2 + 1;
   if (d.Py > fft_max_len<double2>() || d.Pz > fft_max_len<double2>()) {
     set_error("vie_plan_create: cross-section embedding %dx%d exceeds one shared-memory line", d.Py, d.Pz);
@@ -308,6 +325,17 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
     }
   }
   VIE_TRY(fft_get(d.L, &P->fL));
+  if (P->xq > 1) {
+    VIE_TRY(fft_get(d.L / P->xq, &P->fLq));
+    std::vector<float2> tw(d.L);
+    for (int j = 0; j < d.L; ++j) {
+      const double a = -2.0 * M_PI * (double)j / (double)d.L;
+      tw[j] = make_float2((float)cos(a), (float)sin(a));
+    }
+    VIE_TRY(P->twL64.alloc(sizeof(float2) * d.L));
+    VIE_CUDA(cudaMemcpyAsync(P->twL64.p, tw.data(), sizeof(float2) * d.L, cudaMemcpyHostToDevice, P->st));
+    VIE_CUDA(cudaStreamSynchronize(P->st));   // tw lives on this stack frame
+  }
   if (d.L > fft_max_len<float2>() || d.L > fft_max_len<double2>()) {
     const FftLen* h;
     VIE_TRY(fft_get(d.L / 2, &h));   // half length used by the split, cached before any capture
@@ -439,11 +467,14 @@ size_t vie_estimate_bytes(int nx, int ny, int nz, const vie_opts* opts) {
   vie_opts o;
   if (opts) o = *opts; else vie_default_opts(&o);
   const double N = (double)nx * ny * nz;
-  const double L = 2.0 * fft_next_smooth(nx), Py = 2.0 * fft_next_smooth(ny), Pz = 2.0 * fft_next_smooth(nz);
+  int xq = 1;
+  const double L = embed_x(nx, &xq), Py = 2.0 * fft_next_smooth(ny), Pz = 2.0 * fft_next_smooth(nz);
   const double spec = 6.0 * (L / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1) * (16 + 8);
   const double full = L * Py * Pz * 16;                  // spectra assembly scratch
   const double T = 3.0 * Pz * Py * nx * (16 + 8) + ((double)Py * Pz > 4096 ? 3.0 * nz * Py * nx * (16 + 8) : 0);
-  const double Sx = (3.0 * L * 16 > 200 * 1024) ? 3.0 * Pz * Py * L * (16 + 8) : 0;
+  // full x-spectra of the unfused x pass (complex FP32 only without a cluster split)
+  const double Sx = (3.0 * L * 16 > 200 * 1024 ? 3.0 * Pz * Py * L * 16 : 0) +
+                    (3.0 * L * 8 > 200 * 1024 && xq == 1 ? 3.0 * Pz * Py * L * 8 : 0);
   const double Xs = (L > 12736) ? 3.0 * Pz * Py * L * 16 + L * Py * Pz * 16 : 0;   // long-line split scratch
   const double vec = N * 3 * (16 * 6 + 8 * 8) + N * 24;
   const int R = o.precision == VIE_MIXED ? (o.inner_restart > 0 ? o.inner_restart : std::min(2 * o.restart, 128))

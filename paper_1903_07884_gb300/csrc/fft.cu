@@ -232,6 +232,73 @@ __global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
   }
 }
 
+// Bluestein's chirp-z transform of whole lines in one kernel, when the
+// convolution length M fits shared memory: a_i = x_i c_i, FFT_M, times the
+// chirp spectrum, inverse FFT_M, times c_f, with c = conj(b) (forward) or b
+// (inverse) -- the two launches of the staged transform with the M-point
+// intermediate kept in shared memory instead of a global scratch line.
+template <class C, int MAXE>
+__global__ void __launch_bounds__(MAXE == 0 ? 256 : 1024)
+    k_fft_bluestein(const C* __restrict__ in, C* __restrict__ out, LineDesc d, FftPlanDev p, int lpc,
+                    const C* __restrict__ chirp, int cmode, const C* __restrict__ hat, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  using T = typename real_of<C>::type;
+  const int M = p.n;
+  const int pitch = M + 1;
+  const int l0 = blockIdx.x * lpc;
+  const int nl = min(lpc, d.nlines - l0);
+  const int E = nl * M;
+  auto split = [&](int e, int& li, int& i) {
+    if (d.ies == 1) { li = e / M; i = e - li * M; } else { i = e / nl; li = e - i * nl; }
+  };
+  auto cw = [&](int i) {
+    C w = chirp[i];
+    if (cmode == 2) w.y = -w.y;
+    return w;
+  };
+  batched_copy<8>(
+      E,
+      [&](int e) {
+        int li, i;
+        split(e, li, i);
+        C v = czero<C>();
+        if (i < d.n_in) v = cmul(in[line_in_off(d, l0 + li) + (long long)i * d.ies], cw(i));
+        return v;
+      },
+      [&](int e, C v) {
+        int li, i;
+        split(e, li, i);
+        s[li * pitch + i] = v;
+      });
+  __syncthreads();
+  SmemLines L{nl, nl, pitch, 0, 1, 0};
+  C* res = s;
+  if constexpr (MAXE == 0) {
+    res = fft_smem_pp(s, s + (size_t)lpc * pitch, p, L, -1);
+  } else {
+    fft_smem<MAXE>(s, p, L, -1);
+  }
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const int li = e / M, k = e - li * M;
+    res[li * pitch + k] = cmul(res[li * pitch + k], hat[k]);
+  }
+  __syncthreads();
+  if constexpr (MAXE == 0) {
+    res = fft_smem_pp(res, res == s ? s + (size_t)lpc * pitch : s, p, L, +1);
+  } else {
+    fft_smem<MAXE>(s, p, L, +1);
+  }
+  const T sc = (T)scale;
+  const int Eo = nl * d.n_out;
+  for (int e = threadIdx.x; e < Eo; e += blockDim.x) {
+    int li, f;
+    if (d.oes == 1) { li = e / d.n_out; f = e - li * d.n_out; } else { f = e / nl; li = e - f * nl; }
+    const C v = cmul(res[li * pitch + f], cw(f));
+    out[line_out_off(d, l0 + li) + (long long)f * d.oes] = cscale(v, sc);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Power-of-two lines of n = 32 N1 points (N1 = 8, 16, 32) in complex FP32,
 // one warp per G = 32 / N1 lines, the arithmetic in registers.  With input
@@ -458,13 +525,62 @@ static vie_status launch_len(const C* in, C* out, const LineDesc& d, const FftPl
   return VIE_OK;
 }
 
+// One-kernel Bluestein transform of d's lines (M = f.M fits shared memory):
+// the tiling of launch_lines for lines of length M.
+template <class C>
+static vie_status launch_bluestein(const C* in, C* out, const LineDesc& d, const FftLen& f, int sign, double scale,
+                                   cudaStream_t st) {
+  const FftPlanDev& p = plan_n<C>(f);
+  const int M = p.n;
+  if (d.nlines <= 0) return VIE_OK;
+  const C* chirp = Tabs<C>::chirp(f);
+  const C* hat = sign < 0 ? Tabs<C>::hatf(f) : Tabs<C>::hati(f);
+  const int cmode = sign < 0 ? 2 : 1;
+  const size_t line_bytes = (size_t)(M + 1) * sizeof(C);
+  const bool pp = 2 * line_bytes <= 200 * 1024;
+  const size_t budget = pp ? 24 * 1024 : 48 * 1024;
+  int lpc = (int)(budget / line_bytes);
+  if (lpc < 1) lpc = 1;
+  if (lpc > d.nlines) lpc = d.nlines;
+  if (lpc > 64) lpc = 64;
+  const int grid = (d.nlines + lpc - 1) / lpc;
+  Prof pf_(sizeof(C) == 8 ? "fft_bluestein_c64" : "fft_bluestein_c128", st);
+  if (pp) {
+    const size_t smem = 2 * (size_t)lpc * line_bytes;
+    auto kern = k_fft_bluestein<C, 0>;
+    VIE_TRY(smem_optin(kern, smem));
+    kern<<<grid, 256, smem, st>>>(in, out, d, p, lpc, chirp, cmode, hat, scale);
+  } else {
+    const long long E = (long long)lpc * M;
+    int threads = 128;
+    while (threads < 1024 && E > 8LL * threads) threads *= 2;
+    const int per = (int)((E + threads - 1) / threads);
+    const size_t smem = (size_t)lpc * line_bytes;
+    if (per <= 16) {
+      auto kern = k_fft_bluestein<C, 16>;
+      VIE_TRY(smem_optin(kern, smem));
+      kern<<<grid, threads, smem, st>>>(in, out, d, p, lpc, chirp, cmode, hat, scale);
+    } else if (per <= 32) {
+      auto kern = k_fft_bluestein<C, 32>;
+      VIE_TRY(smem_optin(kern, smem));
+      kern<<<grid, threads, smem, st>>>(in, out, d, p, lpc, chirp, cmode, hat, scale);
+    } else {
+      set_error("fft: Bluestein tile of %lld elements too large", E);
+      return VIE_EINVAL;
+    }
+  }
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
 template <class C>
 size_t fft_scratch_elems(const FftLen& f, int nlines) {
+  // a Bluestein line that fits shared memory runs in one kernel and needs no
+  // scratch; a longer one needs its M-point intermediate and the split's
   const size_t len = f.bluestein ? (size_t)f.M : (size_t)f.n;
-  size_t s = 0;
-  if (f.bluestein) s += (size_t)nlines * len;
-  if (len > (size_t)fft_max_len<C>()) s += (size_t)nlines * len;
-  return s;
+  if (len <= (size_t)fft_max_len<C>()) return 0;
+  return (size_t)nlines * len * (f.bluestein ? 2 : 1);
 }
 template size_t fft_scratch_elems<float2>(const FftLen&, int);
 template size_t fft_scratch_elems<double2>(const FftLen&, int);
@@ -479,6 +595,7 @@ vie_status fft_lines(const C* in, C* out, const LineDesc& d, const FftLen& f, in
       return launch_warp_fft((const float2*)in, (float2*)out, d, plan_n<float2>(f), sign, scale, st);
     return launch_len<C>(in, out, d, plan_n<C>(f), sign, nullptr, 0, nullptr, 0, scale, tmp, st);
   }
+  if (f.M <= fft_max_len<C>()) return launch_bluestein<C>(in, out, d, f, sign, scale, st);
   if (!tmp) { set_error("fft: Bluestein length %d needs a scratch buffer", f.n); return VIE_EINVAL; }
   C* split = f.M > fft_max_len<C>() ? tmp + (size_t)d.nlines * f.M : nullptr;
   // step 1: a_k = x_k * conj(b_k) (forward) or x_k * b_k (inverse), FFT_M, times chirp spectrum

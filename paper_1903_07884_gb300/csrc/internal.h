@@ -97,6 +97,12 @@ struct vie_plan_s {
   vie::MvDims d{};
   const vie::FftLen *fL = nullptr, *fPy = nullptr, *fPz = nullptr;
   bool fused_x128 = true, fused_x64 = true;   // fused x-pass fits shared memory
+  // complex-FP32 x pass split over a cluster of xq CTAs (2 or 4; 1 = none):
+  // each CTA transforms every xq-th frequency of the three lines with length
+  // L / xq (fLq) and the twiddles W_L^j, j < L (twL64)
+  int xq = 1;
+  const vie::FftLen* fLq = nullptr;
+  vie::DevBuf twL64;
   // x-pass variant per precision [c64, c128] chosen by the autotuner (-1:
   // untuned, the default rule; 0: compile-time radix-16 kernel; k >= 1: the
   // generic Stockham kernel with radix order xord[.][k - 1])
@@ -193,6 +199,9 @@ vie_status precond_apply(vie_plan_s* P, const C* r, C* z, cudaStream_t st);
 void precond_free(vie_plan_s* P);
 vie_status precond_add_fp64(vie_plan_s* P);
 vie_status precond_set_rep_tile(vie_plan_s* P, int tn);
+// x-embedding length of nx points and the cluster split of its complex-FP32
+// x pass (1, 2 or 4)
+int embed_x(int nx, int* q);
 vie_status box_homogenise(vie_plan_s* P, const vie_box& b, DevBuf& Mt, bool plane);
 vie_status factor_invert_blocks(vie_plan_s* P, DevBuf& LU, int m, int nblk, bool want64, DevBuf* inv64, bool want128,
                                 DevBuf* inv128);

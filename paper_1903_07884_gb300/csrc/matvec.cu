@@ -17,10 +17,12 @@ vie_status matvec_alloc(vie_plan_s* P) {
   P->fused_x128 = (size_t)3 * d.L * sizeof(double2) <= 200 * 1024;
   P->fused_x64 = (size_t)3 * d.L * sizeof(float2) <= 200 * 1024;
   if (!P->fused_x128) VIE_TRY(P->S128.alloc(sizeof(double2) * nS));
-  if (!P->fused_x64) VIE_TRY(P->S64.alloc(sizeof(float2) * nS));
+  // (complex FP32 split over a cluster keeps its lines in shared memory)
+  const bool unfused64 = !P->fused_x64 && P->xq == 1;
+  if (unfused64) VIE_TRY(P->S64.alloc(sizeof(float2) * nS));
   const int nl = 3 * d.Py * d.Pz;
   const size_t x128 = P->fused_x128 ? 0 : fft_scratch_elems<double2>(*P->fL, nl);
-  const size_t x64 = P->fused_x64 ? 0 : fft_scratch_elems<float2>(*P->fL, nl);
+  const size_t x64 = unfused64 ? fft_scratch_elems<float2>(*P->fL, nl) : 0;
   if (x128) VIE_TRY(P->X128.alloc(sizeof(double2) * x128));
   if (x64) VIE_TRY(P->X64.alloc(sizeof(float2) * x64));
   // cross-sections whose Py x Pz slab does not fit shared memory take the

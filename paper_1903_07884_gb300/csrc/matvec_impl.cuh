@@ -16,6 +16,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "prof.h"
 
@@ -84,9 +86,11 @@ __device__ __forceinline__ C spec_at(const C* __restrict__ spec, int c, int kx, 
   return v;
 }
 
+// the 3x3 tensor product on n spectrum points held at k = 0..n-1 of the
+// lines, which are the x-frequencies kx = k0 + kstep k
 template <class C>
 __device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, int kz, const C* __restrict__ spec,
-                                           const MvDims& d) {
+                                           const MvDims& d, int kstep = 1, int k0 = 0) {
   const bool fy = ky > d.Py / 2, fz = kz > d.Pz / 2;
   const int kyo = fy ? d.Py - ky : ky;
   const int kzo = fz ? d.Pz - kz : kz;
@@ -99,8 +103,9 @@ __device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, i
     if (fz) sg *= pair_parity(c, 2);
     syz[c] = sg;
   }
-  for (int kx = threadIdx.x; kx < L; kx += blockDim.x) {
-    const C X0 = s0[kx], X1 = s1[kx], X2 = s2[kx];
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const int kx = k0 + kstep * k;
+    const C X0 = s0[k], X1 = s1[k], X2 = s2[k];
     const C gxx = spec_at(spec, 0, kx, kyo, kzo, syz[0], d, Q);
     const C gxy = spec_at(spec, 1, kx, kyo, kzo, syz[1], d, Q);
     const C gxz = spec_at(spec, 2, kx, kyo, kzo, syz[2], d, Q);
@@ -110,7 +115,7 @@ __device__ __forceinline__ void tensor_mul(C* s0, C* s1, C* s2, int L, int ky, i
     C y0 = cmul(gxx, X0), y1 = cmul(gxy, X0), y2 = cmul(gxz, X0);
     cfma(y0, gxy, X1); cfma(y1, gyy, X1); cfma(y2, gyz, X1);
     cfma(y0, gxz, X2); cfma(y1, gyz, X2); cfma(y2, gzz, X2);
-    s0[kx] = y0; s1[kx] = y1; s2[kx] = y2;
+    s0[k] = y0; s1[k] = y1; s2[k] = y2;
   }
 }
 
@@ -159,6 +164,73 @@ __global__ void __launch_bounds__(MAXE == 0 ? 512 : 1024) k_mv_x(C* __restrict__
     const int a = e / d.nx, i = e - a * d.nx;
     T[a * lstride + loff + i] = res[a * L + i];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fused x pass split over a cluster of Q CTAs (complex FP32), for embeddings
+// whose three lines do not fit one CTA's shared memory.  With Lq = L / Q,
+// CTA r of the cluster of one (ky, kz) forms, by decimation in frequency,
+//   a_r[n] = sum_j x[n + j Lq] W_L^{(n + j Lq) r}   (n < Lq; x = 0 from nx on),
+// whose Lq-point transform is X[Q k + r]; it multiplies those frequencies by
+// the generator spectra and transforms them back to z_r.  The outputs are
+//   y[n] = sum_r W_L^{-n r} z_r[n mod Lq]   (n < nx),
+// each CTA assembling a contiguous share of them from the Q CTAs' shared
+// memory (distributed shared memory of the cluster).
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(512)
+    k_mv_xq(float2* __restrict__ T, const float2* __restrict__ spec, MvDims d, FftPlanDev pl,
+            const float2* __restrict__ twL) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* s = reinterpret_cast<float2*>(smem_raw);
+  const int r = (int)cl.block_rank();
+  const int kyz = blockIdx.x / Q;
+  const int ky = kyz % d.Py, kz = kyz / d.Py;
+  const int L = d.L, Lq = L / Q;
+  const long long lstride = (long long)d.Pz * d.Py * d.nx;
+  const long long loff = ((long long)kz * d.Py + ky) * d.nx;
+  for (int e = threadIdx.x; e < 3 * Lq; e += blockDim.x) {
+    const int b = e / Lq, n = e - b * Lq;
+    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int i = n + j * Lq;
+      if (i < d.nx) {
+        const float2 v = T[b * lstride + loff + i];
+        a = cadd(a, r == 0 ? v : cmul(v, twL[(i * r) % L]));
+      }
+    }
+    s[e] = a;
+  }
+  __syncthreads();
+  const SmemLines Ls{3, 3, Lq, 0, 1, 0};
+  float2* r1 = fft_smem_pp(s, s + 3 * Lq, pl, Ls, -1);
+  tensor_mul(r1, r1 + Lq, r1 + 2 * Lq, Lq, ky, kz, spec, d, Q, r);
+  __syncthreads();
+  float2* res = fft_smem_pp(r1, r1 == s ? s + 3 * Lq : s, pl, Ls, +1);
+  // every CTA's z_r is complete (and visible to the cluster) past this point;
+  // all of them read their inputs from T before it
+  cl.sync();
+  const float2* z[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) z[q] = cl.map_shared_rank(res, q);
+  const int chunk = (d.nx + Q - 1) / Q;
+  const int n0 = r * chunk, cnt = max(0, min(d.nx, n0 + chunk) - n0);
+  for (int e = threadIdx.x; e < 3 * cnt; e += blockDim.x) {
+    const int b = e / cnt, n = n0 + (e - b * cnt);
+    const int nm = n % Lq;
+    float2 y = z[0][b * Lq + nm];
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+      const float2 w = twL[(n * q) % L];
+      y = cadd(y, cmul(z[q][b * Lq + nm], make_float2(w.x, -w.y)));
+    }
+    T[b * lstride + loff + n] = y;
+  }
+  // no CTA leaves (releasing its shared memory) while another still reads it
+  cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -873,10 +945,34 @@ static inline int yz_variant(const MvDims& d) {
 // The x pass alone (pass B of the matvec) in one of its variants: T holds
 // the yz-transformed field on entry and the inverse x-transformed product on
 // exit.  The autotuner times the variants with this entry.
+// the cluster-split x pass (variant 5; the default where P->xq > 1)
+static vie_status xpass_split(vie_plan_s* P, const float2* spec, float2* T, cudaStream_t st) {
+  const MvDims& d = P->d;
+  const int Q = P->xq, Lq = d.L / Q;
+  const size_t smem = 2 * 3 * (size_t)Lq * sizeof(float2);
+  const FftPlanDev pl = planof<float2>(*P->fLq);
+  const float2* tw = P->twL64.as<float2>();
+  Prof pf_("mv_x_c64", st);
+  if (Q == 2) {
+    VIE_TRY(set_smem(k_mv_xq<2>, smem));
+    k_mv_xq<2><<<d.Py * d.Pz * 2, 512, smem, st>>>(T, spec, d, pl, tw);
+  } else {
+    VIE_TRY(set_smem(k_mv_xq<4>, smem));
+    k_mv_xq<4><<<d.Py * d.Pz * 4, 512, smem, st>>>(T, spec, d, pl, tw);
+  }
+  count_launch();
+  VIE_CHECK_LAUNCH();
+  return VIE_OK;
+}
+
 template <class C>
 vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStream_t st) {
   const MvDims& d = P->d;
   const int cap = 16;
+  if constexpr (sizeof(C) == 8) {
+    if (P->xq > 1 && (variant == 5 || variant < 0 || !P->fused_x64))
+      return xpass_split(P, (const float2*)spec, (float2*)T, st);
+  }
   const FftPlanDev plan_of = planof<C>(*P->fL);
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;
   if (fused) {

@@ -24,6 +24,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -127,7 +128,8 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   const FftPlanDev base = pi == 0 ? P->fL->pn32 : P->fL->pn64;
   const int nord = radix_orders(d.L, base, P->xord[pi]);
   const char* tag = pi == 0 ? "x_pass_c64" : "x_pass_c128";
-  if (!fused) return VIE_OK;   // the unfused path transforms through S; nothing to choose
+  const bool split = pi == 0 && P->xq > 1;   // the cluster-split kernel (variant 5) is a candidate
+  if (!fused && !split) return VIE_OK;   // the unfused path transforms through S; nothing to choose
   const TuneKey key{0, pi, d.L, d.Py, d.Pz};
   int choice;
   std::string rep;
@@ -148,8 +150,12 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   rep = buf;
   int best = -1;
   float tbest = 0;
-  for (int v = ct ? 0 : 1; v <= (fp ? 4 : nord); ++v) {
-    if (v > nord && v < 4) continue;
+  std::vector<int> cands;
+  if (ct) cands.push_back(0);
+  for (int v = 1; fused && v <= nord; ++v) cands.push_back(v);
+  if (fp) cands.push_back(4);
+  if (split) cands.push_back(5);
+  for (int v : cands) {
     // an order equal to an earlier one (a palindromic radix list) is not timed twice
     bool dup = false;
     for (int u = 1; v <= 3 && u < v && !dup; ++u) {
@@ -162,6 +168,7 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
     VIE_TRY(time_ms(P->st, 3, [&] { return xpass<C>(P, spec, T, S, v, P->st); }, &ms));
     const std::string name = v == 0   ? std::string(d.L == 2048 ? "radix16x16x8" : "radix16x16x16")
                              : v == 4 ? std::string(d.L == 4096 ? "radix16x16x4x4" : "radix16x16x8x4")
+                             : v == 5 ? "cluster" + std::to_string(P->xq) + "x" + radix_name(P->fLq->pn32)
                                       : radix_name(P->xord[pi][v - 1]);
     snprintf(buf, sizeof(buf), " %s %.4f ms;", name.c_str(), ms);
     rep += buf;
@@ -280,9 +287,10 @@ extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int 
   const MvDims& d = P->d;
   if (k == "x_pass_c64" || k == "x_pass_c128") {
     const bool c64 = k == "x_pass_c64";
-    const bool ok = choice == -1 || (choice >= 1 && choice <= 3) ||
+    const bool fused = c64 ? P->fused_x64 : P->fused_x128;
+    const bool ok = choice == -1 || (choice >= 1 && choice <= 3 && (fused || !c64 || P->xq == 1)) ||
                     (c64 && choice == 0 && (d.L == 2048 || d.L == 4096)) ||
-                    (c64 && choice == 4 && (d.L == 4096 || d.L == 8192));
+                    (c64 && choice == 4 && (d.L == 4096 || d.L == 8192)) || (c64 && choice == 5 && P->xq > 1);
     if (!ok) { set_error("vie_plan_set_tuning: x-pass variant %d does not exist for L = %d", choice, d.L); return VIE_EINVAL; }
     P->xvar[c64 ? 0 : 1] = choice;
   } else if (k == "yz_generic_c64") {

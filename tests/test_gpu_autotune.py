@@ -94,12 +94,15 @@ def test_yz_columns_per_cta_tuned_for_register_cross_sections():
 
 
 @pytest.mark.parametrize("nx,variants", [(1013, [0, 1, 2, 3]), (2031, [0, 1, 2, 3, 4]), (4073, [1, 2, 3, 4]),
-                                         (700, [1, 2, 3])])
+                                         (700, [1, 2, 3]), (2200, [1, 2, 3, 5]), (4500, [5]), (7803, [5])])
 def test_every_x_pass_variant_matches_oracle(nx, variants):
     """Every candidate the tuner may choose, forced in turn through the test
     hook: three-pass (L = 2048, 4096) and four-pass (L = 4096, 8192)
-    compile-time kernels and the generic kernel with each radix order, on
-    ragged lengths (zero padding and crop at non-aligned edges)."""
+    compile-time kernels, the generic kernel with each radix order, and the
+    kernel split over a cluster of CTAs (nx = 2200: two CTAs on L = 4410;
+    nx = 4500 and 7803: four CTAs on L = 9000 and 15680, where one CTA cannot
+    hold the three lines), on ragged lengths (zero padding and crop at
+    non-aligned edges)."""
     cuda_or_fail()
     ny, nz = 3, 2
     eps = inputs.random_permittivity(nz, ny, nx, seed=nx + 5)
@@ -118,9 +121,21 @@ def test_every_x_pass_variant_matches_oracle(nx, variants):
         y = plan.matvec(xd, vie.VIE_FP64).cpu().numpy()
         assert maxerr(y, ref) <= 1e-12, (nx, v)
     # a variant the shape does not have is refused
-    bad = 4 if nx in (1013, 700) else 0 if nx == 4073 else 5
+    bad = {1013: 4, 700: 4, 4073: 0, 2031: 5, 2200: 4, 4500: 1, 7803: 1}[nx]
     assert vie.vie_plan_set_tuning(plan.handle, "x_pass_c64", bad) == vie.VIE_EINVAL
     plan.close()
+
+
+@pytest.mark.parametrize("nx,q", [(2200, 2), (4500, 4)])
+def test_cluster_split_x_pass_is_a_tuned_candidate(nx, q):
+    """Embeddings whose three complex-FP32 lines exceed one CTA's shared
+    memory are timed with the x pass split over a cluster of q CTAs (and, where
+    one CTA still fits them, against the generic kernel)."""
+    cuda_or_fail()
+    plan = Plan(nx, 4, 2, 0.025, K0, 1.0, make_opts(precision=vie.VIE_MIXED, precond=vie.VIE_PREC_NONE))
+    lines = _xpass_lines(vie.vie_plan_tuning(plan.handle), "x_pass_c64")
+    plan.close()
+    assert len(lines) == 1 and f" cluster{q}x" in lines[0], lines
 
 
 def test_every_yz_and_gemv_choice_matches_oracle():
