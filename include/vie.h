@@ -282,9 +282,9 @@ const char* vie_plan_tuning(vie_plan_t plan);
  * "x_pass_c64" / "x_pass_c128" with choice -1 (default rule), 0 (three-pass
  * compile-time kernel, complex FP32, L = 2048 or 4096), 1..3 (generic
  * Stockham kernel with radix order 1..3), 4 (four-pass compile-time kernel,
- * complex FP32, L = 4096 or 8192) or 5 (complex FP32: the x pass split over a
- * cluster of 2 or 4 CTAs, for embeddings whose three lines do not fit one
- * CTA's shared memory); "yz_passes_c64" with 16, 8 or 4 x-columns
+ * complex FP32, L = 4096 or 8192) or 5, 6, 7 (complex FP32: the x pass split
+ * over a cluster of 2, 4 or 8 CTAs, for embeddings whose three lines do not
+ * fit one CTA's shared memory; at least the smallest split that fits); "yz_passes_c64" with 16, 8 or 4 x-columns
  * per CTA of the register yz passes; "yz_generic_c64" with 1, 2, 4, 8 or 16
  * x-columns per CTA of the generic yz passes (as shared memory allows);
  * "block_gemv" with 1, 2, 4 or 8 CTAs per kept block, "rep_gemm_tc" with

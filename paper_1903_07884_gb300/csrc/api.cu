@@ -100,18 +100,19 @@ static int embed_len(int n) { return 2 * fft_next_smooth(n); }
 
 // x-embedding (any L >= 2 nx - 1 gives the same matvec): 2 smooth(nx), whose
 // three complex-FP32 lines one CTA transforms when they fit shared memory
-// (or L = 4096, 8192, the compile-time kernels); past that the x pass splits
-// the frequencies over a cluster of 2 CTAs (lines of L/2), then of 4 CTAs
-// with L = 4 smooth(ceil(nx / 2)) >= 2 nx (lines of L/4); beyond that the
-// unfused path through the full x-spectrum.
+// (or L = 4096, 8192, the compile-time kernels); past that
+// L = 8 smooth(ceil(nx / 4)) >= 2 nx, a multiple of 8, and the x pass splits
+// the frequencies over a cluster of Q = 2, 4 or 8 CTAs (lines of L/Q; *q is
+// the smallest Q that fits, the autotuner may take a larger one); beyond
+// that the unfused path through the full x-spectrum.
 int embed_x(int nx, int* q) {
   const int L = embed_len(nx);
   const int lq_max = (int)((200 * 1024) / (2 * 3 * sizeof(float2)));   // three lines, two copies
   *q = 1;
   if (L <= lq_max || L == 4096 || L == 8192) return L;
-  if (L / 2 <= lq_max) { *q = 2; return L; }
-  const int L4 = 4 * fft_next_smooth((nx + 1) / 2);
-  if (L4 / 4 <= lq_max) { *q = 4; return L4; }
+  const int L8 = 8 * fft_next_smooth((nx + 3) / 4);
+  for (int Q = 2; Q <= 8; Q *= 2)
+    if (L8 / Q <= lq_max) { *q = Q; return L8; }
   return L;
 }
 
@@ -326,7 +327,8 @@ vie_status vie_plan_create(int nx, int ny, int nz, double h, double k0, double e
   }
   VIE_TRY(fft_get(d.L, &P->fL));
   if (P->xq > 1) {
-    VIE_TRY(fft_get(d.L / P->xq, &P->fLq));
+    for (int Q = P->xq, i = P->xq == 2 ? 0 : P->xq == 4 ? 1 : 2; Q <= 8; Q *= 2, ++i)
+      VIE_TRY(fft_get(d.L / Q, &P->fLq[i]));
     std::vector<float2> tw(d.L);
     for (int j = 0; j < d.L; ++j) {
       const double a = -2.0 * M_PI * (double)j / (double)d.L;

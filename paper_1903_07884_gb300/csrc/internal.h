@@ -97,11 +97,12 @@ struct vie_plan_s {
   vie::MvDims d{};
   const vie::FftLen *fL = nullptr, *fPy = nullptr, *fPz = nullptr;
   bool fused_x128 = true, fused_x64 = true;   // fused x-pass fits shared memory
-  // complex-FP32 x pass split over a cluster of xq CTAs (2 or 4; 1 = none):
-  // each CTA transforms every xq-th frequency of the three lines with length
-  // L / xq (fLq) and the twiddles W_L^j, j < L (twL64)
+  // complex-FP32 x pass split over a cluster of Q CTAs (Q = 2, 4 or 8; xq is
+  // the smallest Q whose lines fit shared memory, 1 = no split): each CTA
+  // transforms every Q-th frequency of the three lines with length L / Q
+  // (fLq[log2 Q - 1]) and the twiddles W_L^j, j < L (twL64)
   int xq = 1;
-  const vie::FftLen* fLq = nullptr;
+  const vie::FftLen* fLq[3] = {nullptr, nullptr, nullptr};
   vie::DevBuf twL64;
   // x-pass variant per precision [c64, c128] chosen by the autotuner (-1:
   // untuned, the default rule; 0: compile-time radix-16 kernel; k >= 1: the

@@ -945,20 +945,26 @@ static inline int yz_variant(const MvDims& d) {
 // The x pass alone (pass B of the matvec) in one of its variants: T holds
 // the yz-transformed field on entry and the inverse x-transformed product on
 // exit.  The autotuner times the variants with this entry.
-// the cluster-split x pass (variant 5; the default where P->xq > 1)
-static vie_status xpass_split(vie_plan_s* P, const float2* spec, float2* T, cudaStream_t st) {
+// the cluster-split x pass with Q = 2, 4 or 8 CTAs per line triple
+// (variants 5, 6, 7; Q = P->xq, the smallest that fits, by default)
+static vie_status xpass_split(vie_plan_s* P, int Q, const float2* spec, float2* T, cudaStream_t st) {
   const MvDims& d = P->d;
-  const int Q = P->xq, Lq = d.L / Q;
+  const int qi = Q == 2 ? 0 : Q == 4 ? 1 : 2;
+  if (Q < P->xq || Q > 8 || d.L % Q || !P->fLq[qi]) { set_error("matvec: no %d-CTA split for L = %d", Q, d.L); return VIE_EINVAL; }
+  const int Lq = d.L / Q;
   const size_t smem = 2 * 3 * (size_t)Lq * sizeof(float2);
-  const FftPlanDev pl = planof<float2>(*P->fLq);
+  const FftPlanDev pl = planof<float2>(*P->fLq[qi]);
   const float2* tw = P->twL64.as<float2>();
   Prof pf_("mv_x_c64", st);
   if (Q == 2) {
     VIE_TRY(set_smem(k_mv_xq<2>, smem));
     k_mv_xq<2><<<d.Py * d.Pz * 2, 512, smem, st>>>(T, spec, d, pl, tw);
-  } else {
+  } else if (Q == 4) {
     VIE_TRY(set_smem(k_mv_xq<4>, smem));
     k_mv_xq<4><<<d.Py * d.Pz * 4, 512, smem, st>>>(T, spec, d, pl, tw);
+  } else {
+    VIE_TRY(set_smem(k_mv_xq<8>, smem));
+    k_mv_xq<8><<<d.Py * d.Pz * 8, 512, smem, st>>>(T, spec, d, pl, tw);
   }
   count_launch();
   VIE_CHECK_LAUNCH();
@@ -970,8 +976,8 @@ vie_status xpass(vie_plan_s* P, const C* spec, C* T, C* S, int variant, cudaStre
   const MvDims& d = P->d;
   const int cap = 16;
   if constexpr (sizeof(C) == 8) {
-    if (P->xq > 1 && (variant == 5 || variant < 0 || !P->fused_x64))
-      return xpass_split(P, (const float2*)spec, (float2*)T, st);
+    if (P->xq > 1 && (variant >= 5 || variant < 0 || !P->fused_x64))
+      return xpass_split(P, variant >= 5 ? 1 << (variant - 4) : P->xq, (const float2*)spec, (float2*)T, st);
   }
   const FftPlanDev plan_of = planof<C>(*P->fL);
   const bool fused = sizeof(C) == 16 ? P->fused_x128 : P->fused_x64;

@@ -128,7 +128,7 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   const FftPlanDev base = pi == 0 ? P->fL->pn32 : P->fL->pn64;
   const int nord = radix_orders(d.L, base, P->xord[pi]);
   const char* tag = pi == 0 ? "x_pass_c64" : "x_pass_c128";
-  const bool split = pi == 0 && P->xq > 1;   // the cluster-split kernel (variant 5) is a candidate
+  const bool split = pi == 0 && P->xq > 1;   // the cluster-split kernels (variants 5..7) are candidates
   if (!fused && !split) return VIE_OK;   // the unfused path transforms through S; nothing to choose
   const TuneKey key{0, pi, d.L, d.Py, d.Pz};
   int choice;
@@ -154,7 +154,7 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
   if (ct) cands.push_back(0);
   for (int v = 1; fused && v <= nord; ++v) cands.push_back(v);
   if (fp) cands.push_back(4);
-  if (split) cands.push_back(5);
+  for (int Q = P->xq; split && Q <= 8; Q *= 2) cands.push_back(4 + (Q == 2 ? 1 : Q == 4 ? 2 : 3));
   for (int v : cands) {
     // an order equal to an earlier one (a palindromic radix list) is not timed twice
     bool dup = false;
@@ -168,7 +168,7 @@ static vie_status tune_x(vie_plan_s* P, int pi) {
     VIE_TRY(time_ms(P->st, 3, [&] { return xpass<C>(P, spec, T, S, v, P->st); }, &ms));
     const std::string name = v == 0   ? std::string(d.L == 2048 ? "radix16x16x8" : "radix16x16x16")
                              : v == 4 ? std::string(d.L == 4096 ? "radix16x16x4x4" : "radix16x16x8x4")
-                             : v == 5 ? "cluster" + std::to_string(P->xq) + "x" + radix_name(P->fLq->pn32)
+                             : v >= 5 ? "cluster" + std::to_string(1 << (v - 4)) + "x" + radix_name(P->fLq[v - 5]->pn32)
                                       : radix_name(P->xord[pi][v - 1]);
     snprintf(buf, sizeof(buf), " %s %.4f ms;", name.c_str(), ms);
     rep += buf;
@@ -290,7 +290,7 @@ extern "C" vie_status vie_plan_set_tuning(vie_plan_t P, const char* kernel, int 
     const bool fused = c64 ? P->fused_x64 : P->fused_x128;
     const bool ok = choice == -1 || (choice >= 1 && choice <= 3 && (fused || !c64 || P->xq == 1)) ||
                     (c64 && choice == 0 && (d.L == 2048 || d.L == 4096)) ||
-                    (c64 && choice == 4 && (d.L == 4096 || d.L == 8192)) || (c64 && choice == 5 && P->xq > 1);
+                    (c64 && choice == 4 && (d.L == 4096 || d.L == 8192)) || (c64 && choice >= 5 && choice <= 7 && P->xq > 1 && (1 << (choice - 4)) >= P->xq);
     if (!ok) { set_error("vie_plan_set_tuning: x-pass variant %d does not exist for L = %d", choice, d.L); return VIE_EINVAL; }
     P->xvar[c64 ? 0 : 1] = choice;
   } else if (k == "yz_generic_c64") {

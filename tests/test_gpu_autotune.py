@@ -94,15 +94,16 @@ def test_yz_columns_per_cta_tuned_for_register_cross_sections():
 
 
 @pytest.mark.parametrize("nx,variants", [(1013, [0, 1, 2, 3]), (2031, [0, 1, 2, 3, 4]), (4073, [1, 2, 3, 4]),
-                                         (700, [1, 2, 3]), (2200, [1, 2, 3, 5]), (4500, [5]), (7803, [5])])
+                                         (700, [1, 2, 3]), (2200, [1, 2, 3, 5, 6, 7]), (4500, [6, 7]),
+                                         (7803, [6, 7])])
 def test_every_x_pass_variant_matches_oracle(nx, variants):
     """Every candidate the tuner may choose, forced in turn through the test
     hook: three-pass (L = 2048, 4096) and four-pass (L = 4096, 8192)
     compile-time kernels, the generic kernel with each radix order, and the
-    kernel split over a cluster of CTAs (nx = 2200: two CTAs on L = 4410;
-    nx = 4500 and 7803: four CTAs on L = 9000 and 15680, where one CTA cannot
-    hold the three lines), on ragged lengths (zero padding and crop at
-    non-aligned edges)."""
+    kernel split over a cluster of 2, 4 or 8 CTAs (nx = 2200: L = 4480, where
+    one CTA still holds the three lines; nx = 4500 and 7803: L = 9000 and
+    15680, where it needs at least four), on ragged lengths (zero padding and
+    crop at non-aligned edges)."""
     cuda_or_fail()
     ny, nz = 3, 2
     eps = inputs.random_permittivity(nz, ny, nx, seed=nx + 5)
@@ -121,7 +122,7 @@ def test_every_x_pass_variant_matches_oracle(nx, variants):
         y = plan.matvec(xd, vie.VIE_FP64).cpu().numpy()
         assert maxerr(y, ref) <= 1e-12, (nx, v)
     # a variant the shape does not have is refused
-    bad = {1013: 4, 700: 4, 4073: 0, 2031: 5, 2200: 4, 4500: 1, 7803: 1}[nx]
+    bad = {1013: 4, 700: 4, 4073: 0, 2031: 5, 2200: 4, 4500: 5, 7803: 1}[nx]
     assert vie.vie_plan_set_tuning(plan.handle, "x_pass_c64", bad) == vie.VIE_EINVAL
     plan.close()
 
