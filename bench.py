@@ -997,6 +997,24 @@ def run_profile_case(args):
     return 0
 
 
+def run_profile_request(args):
+    """Create the plan of request args.profile_request of the 256-request
+    serving stream and run one mixed solve of it, nothing else (for ncu
+    captures of the kernels a serving request takes).  Prints one JSON line
+    (not a bench line)."""
+    from paper_1903_07884_gb300 import inputs, vie
+    from paper_1903_07884_gb300.solver import Plan, to_device
+    r = inputs.serving_stream(256)[args.profile_request]
+    p = r.problem()
+    plan = Plan.for_problem(p, precision=vie.VIE_MIXED, tol=args.tol)
+    plan.set_permittivity(to_device(p.eps))
+    _, info = plan.solve(to_device(p.e_inc))
+    plan.close()
+    print(json.dumps({"profile_request": args.profile_request, "grid": [p.nx, p.ny, p.nz], "kind": r.kind,
+                      "iters": info["iters_inner"], "relres": info["relres"]}))
+    return 0
+
+
 def run_precond2_case(args):
     """Blocked disk preconditioner (reduced 1-level bus box + 2-level disk box,
     3 um radius, 20 nm voxels, complex-FP32 apply): per-kernel device times of
@@ -1064,6 +1082,8 @@ def main():
     ap.add_argument("--fp64-serial-n", type=int, default=16, help="requests of the serial FP64 serving leg")
     ap.add_argument("--mixed-serial-n", type=int, default=0,
                     help="requests solved one by one with the mixed method outside the server (0 = skip)")
+    ap.add_argument("--profile-request", type=int, default=None,
+                    help="one mixed solve of that request of the serving stream and nothing else (for ncu captures)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one mixed solve of the workload and nothing else (for ncu captures; prints no bench line)")
     ap.add_argument("--study", choices=["bragg", "bragg_bench_shape", "length", "disk"], default=None,
@@ -1082,6 +1102,8 @@ def main():
         return run_profile_case(args)
     if args.precond2_case:
         return run_precond2_case(args)
+    if args.profile_request is not None:
+        return run_profile_request(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "coupler_batch":

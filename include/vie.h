@@ -130,6 +130,9 @@ void vie_default_opts(vie_opts* opts);
  * NULL (defaults).  Boxes must lie inside the grid and not overlap.
  * Cross-sections whose embedding Py x Pz exceeds 4096 points take the y and z
  * transforms of the matvec as separate line passes (one more work array).
+ * The x-embedding is 2 smooth(nx) (smooth: the next 2-3-5-7-smooth integer),
+ * or 8 smooth(ceil(nx/4)) where the complex-FP32 x pass splits over a
+ * cluster of CTAs (every L >= 2 nx - 1 gives the same product).
  * Errors: VIE_EINVAL for non-positive sizes, h, k0 or eps_bg, boxes out of
  * range / overlapping, box levels outside 0..2, 3*nx*ny*nz >= 2^31 - 64, an
  * embedding or box length beyond the transform limits, and, when a
